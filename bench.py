@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 mDPD hot path: particle-steps/s (and pair-evals/s).
+
+One bench step = one velocity-Verlet time step of the whole hot path (binning,
+density pass, force pass fused with the half-kicks, drift and reflection, FP64
+reductions) over the synthetic workload.  Prints one JSON line.
+
+  python bench.py [--gpus N --steps K --warmup W] [--workload slab|bulk|slit|rock]
+                  [--precision fp32|fp64] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the reference arm of this
+build) on a bounded sample of the same workload on the host cores.
+Multi-GPU (torchrun): each rank advances an independent replica (the path is
+replicated, not sharded); value = all ranks' particle-steps / slowest rank.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2 ** 20
+ISSUE_LANES_PER_SM_CLK = 128          # 4 schedulers x 32 lanes, one instruction each per clock
+NUM_SMS = 152
+# Hand count of the FP32/INT32 lane operations one pair evaluation needs by its
+# formula (Sec. 2.1, Eq. 1): separation 3, r^2 3, cutoff test 1, rsqrt 1, r 1,
+# w_C 1, A term 1, rho_i+rho_j 1, w_d 1, B term 2, v_ij 3, e.v 4, F^D 3,
+# Philox-4x32-10 ten rounds of 2 mul-hi + 2 mul-lo + 2 xor = 60, counter 2,
+# xi 4, F^R 3, sum 2, scale 1, accumulate 3.
+OPS_PER_PAIR = 100
+
+DESC = {
+    "slab": "liquid-vapour slab, periodic 60x20x20, 20x20x20 liquid block at density 6, "
+            "N=48000, A=-40 B=25 gamma=4.5 kT=1 rc=1 rd=0.75 dt=0.01",
+    "bulk": "bulk liquid, periodic 10x10x10, N=6000 uniform random, A=-40 B=25 "
+            "gamma=4.5 kT=1 rc=1 rd=0.75 dt=0.01",
+    "slit": "slit pore 100x40 periodic x,y, height 20, walls from a voxel mask "
+            "(voxel 0.5, 1 rc shell at density 6, A_fs=-30), g_x=0.02, fluid density 6",
+    "rock": "synthetic porous rock, 256^3 voxel Gaussian random field (corr 4 voxels) at "
+            "porosity 0.15, voxel 0.5 rc, 1 rc wall shell at density 6, fluid density 6, g_x=0.01",
+}
+
+
+def make_workload(name: str, precision: int, seed: int):
+    from paper_1903_10134_gb300 import inputs as I
+    if name == "bulk":
+        return I.bulk(seed=seed, precision=precision)
+    if name == "slab":
+        return I.slab(seed=seed, precision=precision)
+    if name == "slit":
+        return I.slit(seed=seed, precision=precision)
+    if name == "rock":
+        return I.rock(seed=seed, precision=precision)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def oracle_throughput(w, budget_s: float, max_steps: int = 1000):
+    """Time the FP64 oracle on the workload: particle-steps/s over a bounded
+    number of steps (at least one) chosen to fill about budget_s seconds."""
+    from oracle import oracle as O
+    walls = _oracle_walls(w)
+    t0 = time.perf_counter()
+    o = O.Oracle(w.params.copy(), w.pos, w.vel, w.type, w.seed, use_cells=True, **walls)
+    setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    o.run(1)
+    one = time.perf_counter() - t0
+    steps = int(max(0, min(max_steps - 1, (budget_s - one) / max(one, 1e-6))))
+    t1 = time.perf_counter()
+    if steps:
+        o.run(steps)
+    el = time.perf_counter() - t1 + one
+    total = steps + 1
+    return {"value": o.n * total / el, "steps": total, "seconds": el, "setup_s": setup,
+            "cores": O.num_threads(), "n": o.n}
+
+
+def _oracle_walls(w) -> dict:
+    """Wall particles and mask for the oracle (its own packing of the image)."""
+    if w.mask is None:
+        return {}
+    import numpy as np
+    from oracle import oracle as O
+    wpos, _ = O.place_walls(w.mask, w.params.periodic, w.voxel, w.origin, w.wall_density,
+                            w.shell, w.wall_seed)
+    w.pos = np.concatenate([w.pos, wpos])
+    w.vel = np.concatenate([w.vel, np.zeros_like(wpos)])
+    w.type = np.concatenate([w.type, np.full(len(wpos), w.wall_type, np.int32)])
+    w.mask_applied = True
+    return {"mask": w.mask, "voxel": w.voxel, "origin": w.origin}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores, same workload: W warm-up steps and up
+    to K timed steps, stopped early once about args.ref_seconds have been spent
+    (the bounded sample is stated in the output)."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    w = make_workload(args.workload, 0, seed=1)
+    walls = _oracle_walls(w)
+    o = O.Oracle(w.params.copy(), w.pos, w.vel, w.type, w.seed, use_cells=True, **walls)
+    t0 = time.perf_counter()
+    for _ in range(args.warmup):
+        o.run(1)
+        if time.perf_counter() - t0 > args.ref_seconds / 4:
+            break
+    done, el = 0, 0.0
+    while done < args.steps and (done == 0 or el < args.ref_seconds):
+        t1 = time.perf_counter()
+        o.run(1)
+        el += time.perf_counter() - t1
+        done += 1
+    value = o.n * done / el
+    sample = (f"{done} of {args.steps} timed FP64 oracle steps of the full {args.workload} "
+              f"workload (N={o.n}), {el:.1f} s")
+    line = {
+        "impl": "reference", "metric": "particle-steps/s", "value": value,
+        "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / done,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "desc": DESC[args.workload], "n": o.n,
+                   "precision": "fp64"},
+        "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": O.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1903_10134_gb300 import mdpd
+
+    dev = torch.cuda.current_device()
+    prec = 0 if args.precision == "fp64" else 1
+    w = make_workload(args.workload, prec, seed=1 + rank)
+    stream = torch.cuda.Stream()
+    s = mdpd.System.from_workload(w, stream=stream)
+    n = s.n
+    working_set = n * (16 + 16 + 4 + 4 + 2 * 3 * 24 + 8)
+    flush = working_set < 4 * L2_BYTES
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if flush else None
+
+    def l2_flush():
+        with torch.cuda.stream(stream):
+            flush_buf.fill_(1.0)
+
+    # warm-up (also captures the step graphs)
+    for _ in range(max(args.warmup, 3)):
+        s.step(1)
+    s.step(2)
+    s.sync()
+    pairs = s.pair_count()
+
+    K = args.steps
+    s.set_option(mdpd.OPT_PROFILE, K)
+    clocks = ClockSampler(dev) if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    if flush:
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+        for k in range(K):
+            l2_flush()
+            starts[k].record(stream)
+            s.step(1)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    else:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    s.sync()
+    prof, prof_steps, launches = s.profile()
+
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * n * K / (ms_max * 1e-3)
+
+    # end-to-end through the host-pointer C ABI: per step upload x, v from
+    # pinned host memory, one step, read x, v back into pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        x, v, _, _ = s.state()
+        hx = torch.from_numpy(x).pin_memory().numpy()
+        hv = torch.from_numpy(v).pin_memory().numpy()
+        ke = max(3, min(K, 200))
+        for _ in range(2):
+            mdpd.mdpd_set_state(s.h, hx, hv)
+            s.step(1)
+            mdpd.mdpd_get_state(s.h, hx, hv, want_type=False, want_rho=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            mdpd.mdpd_set_state(s.h, hx, hv)
+            s.step(1)
+            mdpd.mdpd_get_state(s.h, hx, hv, want_type=False, want_rho=False)
+        el = time.perf_counter() - t0
+        et = torch.tensor([el], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": world * n * ke / float(et.item()), "unit": "particle-steps/s",
+               "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
+               "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes),
+               "steps": ke, "api": "mdpd_set_state + mdpd_step(1) + mdpd_get_state"}
+
+    if rank == 0:
+        peaks = measured_peaks()
+        clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = NUM_SMS * ISSUE_LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e12     # Tlane-op/s
+        force_ms = prof.get("force", 0.0) / max(prof_steps, 1)
+        achieved = (pairs * OPS_PER_PAIR) / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
+        # HBM view of the same kernel: algorithmic bytes per particle of the fused
+        # force pass (FP32 tiles 16+16+4 read, FP64 x, v read and written 96)
+        bytes_pp = (36 if prec == 1 else 68) + 96
+        hbm_peak = peaks.get("hbm_gbs", 6790.0)
+        hbm_ach = n * bytes_pp / (force_ms * 1e-3) / 1e9 if force_ms > 0 else None
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", f"force_traffic_{args.workload}.json")
+        if os.path.exists(tfile):
+            try:
+                traffic = json.load(open(tfile)).get("dram_bytes_per_launch")
+            except (OSError, ValueError):
+                traffic = None
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            wc = make_workload(args.workload, 0, seed=1)
+            info = oracle_throughput(wc, args.cpu_seconds, max_steps=200)
+            cpu = {"value": info["value"], "unit": "particle-steps/s", "cores": info["cores"],
+                   "kind": "oracle",
+                   "sample": f"{info['steps']} FP64 oracle steps of the full {args.workload} "
+                             f"workload (N={info['n']}), {info['seconds']:.1f} s"}
+        line = {
+            "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
+            "n_gpus": world, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": DESC[args.workload], "n": n,
+                       "precision": args.precision,
+                       "l2": "flushed between timed steps" if flush else "working set > L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "pair_evals_per_s": value * pairs / 2 / n,
+            "roofline": {"bound": "alu", "kernel": "force pass (k_force, fused VV)",
+                         "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
+                         "frac": (achieved / alu_peak) if achieved else None,
+                         "peak_note": "152 SMs x 128 lanes x sm_max_mhz (recipe clocks)",
+                         "traffic": traffic,
+                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm_peak,
+                                 "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
+                                 "bytes_per_particle": bytes_pp, "peak_of": "measured"}},
+            "kernel_ms_per_step": {k: v / max(prof_steps, 1) for k, v in prof.items()},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    s.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=tuple(DESC), default="slab")
+    ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-seconds", type=float, default=60.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * mdpd.h -- C ABI of the GB300 (sm_103a) many-body DPD hot path.
+ *
+ * Method: many-body dissipative particle dynamics (mDPD) as used in
+ * arXiv:1903.10134.  Per time step the library bins the particles into a cell
+ * lattice, evaluates the local density rho_i (Sec. 2.1), the pair forces
+ * F^C + F^D + F^R of Sec. 2.1 and Eq. 1, and advances the velocity-Verlet
+ * integrator in the order of Algorithm 1, reflecting particles off solid
+ * voxels of a pore image (Sec. 2.2) and off non-periodic box faces.
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (MDPD_OK) on success or a negative MDPD_ERR_* code; the text of
+ *     the last error of a handle is available from mdpd_last_error().
+ *   - Host arrays are read or written before the call returns (inputs are
+ *     copied, the caller keeps ownership).  *_dev variants take device
+ *     pointers on the current CUDA device, borrowed for the duration of the
+ *     call; their copies are ordered on the handle's stream.
+ *   - Particle arrays are indexed by particle id: the caller's input order is
+ *     0..n-1; wall particles added by mdpd_set_walls() follow as n, n+1, ...
+ *     Vectors are interleaved xyz (element 3*i+k).
+ *   - Units are DPD units with particle mass m = 1.
+ *   - Work is enqueued on the handle's stream; errors raised on the device
+ *     (non-finite values, particles outside a non-periodic box) are reported
+ *     by the next call that synchronises (mdpd_sync, mdpd_get_state,
+ *     mdpd_forces, mdpd_observables*).
+ *   - A handle is used by one host thread at a time.
+ */
+#ifndef MDPD_H
+#define MDPD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDPD_MAX_TYPES 8
+#define MDPD_NUM_OBS 16
+
+enum {
+    MDPD_OK = 0,
+    MDPD_ERR_INVALID_ARG = -1,   /* bad argument or unsupported geometry     */
+    MDPD_ERR_OOM = -2,           /* device or host allocation failed         */
+    MDPD_ERR_CUDA = -3,          /* a CUDA runtime call failed               */
+    MDPD_ERR_NONFINITE = -4,     /* a position, velocity or force is NaN/inf */
+    MDPD_ERR_OUT_OF_BOX = -5,    /* a particle left a non-periodic box       */
+    MDPD_ERR_TILE_OVERFLOW = -6, /* a cell held more particles than a kernel
+                                    tile can stage                           */
+    MDPD_ERR_TIMEOUT = -7        /* a bounded device wait gave up            */
+};
+
+/* System parameters (Sec. 2.1, Eq. 1).  Pair tables are indexed [type_i][type_j]
+ * and must be symmetric.  sigma of the random force follows the
+ * fluctuation-dissipation theorem, sigma^2 = 2 gamma kT (Sec. 2.1). */
+typedef struct mdpd_params {
+    double box_lo[3];        /* lower box corner                                */
+    double box[3];           /* box edge lengths; periodic axes need >= 3 r_c    */
+    int32_t periodic[3];     /* 1 periodic, 0 reflecting faces                  */
+    int32_t ntypes;          /* 1..MDPD_MAX_TYPES                               */
+    double rc;               /* cutoff of w_C = w_R = 1 - r/r_c                 */
+    double rd;               /* many-body cutoff r_d < r_c (w_d, w_rho)         */
+    double dt;               /* time step                                       */
+    double kT;               /* temperature                                     */
+    double A[MDPD_MAX_TYPES][MDPD_MAX_TYPES];     /* attraction, A < 0          */
+    double B[MDPD_MAX_TYPES][MDPD_MAX_TYPES];     /* many-body repulsion, B > 0 */
+    double gamma[MDPD_MAX_TYPES][MDPD_MAX_TYPES]; /* dissipation                */
+    double g[3];             /* body acceleration on mobile particles           */
+    uint32_t frozen_type_mask; /* bit t: type t is frozen (no motion, v = 0)    */
+    int32_t precision;       /* 0: FP64 pair arithmetic; 1: FP32 pair arithmetic
+                                on cell-relative offsets, FP64 integration     */
+    int32_t xi_dist;         /* 0: xi uniform, unit variance; 1: Gaussian       */
+    int32_t rho_self;        /* 1: rho_i also counts w_rho(0) for j = i (0 in
+                                the paper, Sec. 2.1)                           */
+} mdpd_params;
+
+typedef struct mdpd_handle mdpd_handle;
+
+/* Create a system of n particles on the current CUDA device.
+ * pos, vel: host arrays of 3n doubles; type: n values in [0, ntypes).
+ * seed keys the Philox-4x32-10 stream of the random force; the pair draw
+ * for the force evaluation of step s uses counter (min id, max id, s_lo, s_hi)
+ * so that xi_ij = xi_ji (Sec. 2.1).  cuda_stream: a cudaStream_t to run on,
+ * or NULL for a stream the handle creates and owns.
+ * The density and forces of the initial state are evaluated (step index 0).
+ * Errors: INVALID_ARG (n < 0, ntypes out of range, r_d > r_c, non-positive
+ * dt/r_c/box, a periodic axis shorter than 3 r_c, a type out of range),
+ * OOM, CUDA. */
+int mdpd_create(const mdpd_params* params, int64_t n, const double* pos,
+                const double* vel, const int32_t* type, uint64_t seed,
+                void* cuda_stream, mdpd_handle** out);
+
+/* Same as mdpd_create with device arrays pos, vel (3n doubles) and type (n). */
+int mdpd_create_dev(const mdpd_params* params, int64_t n, const double* pos,
+                    const double* vel, const int32_t* type, uint64_t seed,
+                    void* cuda_stream, mdpd_handle** out);
+
+/* Walls from a voxel image (Sec. 2.2, 2.3).  solid: nx*ny*nz bytes, x
+ * fastest, nonzero = solid, covering [origin, origin + n*voxel) per axis.
+ * 1) The image becomes the reflection mask: a drift that lands in a solid
+ *    voxel is undone and the half-step velocity negated.
+ * 2) Solid voxels whose centre lies within shell_thickness of a pore voxel
+ *    centre (periodic wrap on periodic axes) receive wall particles of
+ *    wall_type (which should be frozen) at number density wall_density: a
+ *    voxel gets floor(wall_density * voxel^3 + u) particles at uniform points,
+ *    u and the points drawn from Philox-4x32-10 keyed by seed with counter
+ *    (voxel id, k, 0x57414C4C, 0); they take ids n, n+1, ... by ascending
+ *    voxel id.  Their velocity is 0.
+ * May be called once per handle.  Densities and forces are re-evaluated.
+ * Errors: INVALID_ARG (dims, voxel, type, a periodic axis the image does not
+ * span exactly, a second call), OOM, CUDA. */
+int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
+                   int32_t nz, double voxel, const double origin[3],
+                   double wall_density, double shell_thickness, int32_t wall_type,
+                   uint64_t seed);
+
+/* Advance nsteps velocity-Verlet steps (Algorithm 1 without its
+ * communication lines): v += dt/2 a; x += dt v; reflect; rho(x); a(x, v, rho);
+ * v += dt/2 a.  Asynchronous on the handle's stream.  nsteps >= 0. */
+int mdpd_step(mdpd_handle* h, int64_t nsteps);
+
+/* Wait for the handle's stream and report device-side errors. */
+int mdpd_sync(mdpd_handle* h);
+
+/* Number of particles (including wall particles) and of steps taken. */
+int mdpd_num_particles(const mdpd_handle* h, int64_t* n);
+int mdpd_step_count(const mdpd_handle* h, int64_t* steps);
+
+/* Copy the state to host arrays in id order: pos/vel 3N doubles, type N,
+ * rho N (the local density of the last force evaluation).  Any pointer may
+ * be NULL.  Synchronises. */
+int mdpd_get_state(mdpd_handle* h, double* pos, double* vel, int32_t* type,
+                   double* rho);
+
+/* Device-array variant of mdpd_get_state (no host synchronisation beyond the
+ * error check). */
+int mdpd_get_state_dev(mdpd_handle* h, double* pos, double* vel, int32_t* type,
+                       double* rho);
+
+/* Replace positions and velocities (3N doubles each, id order, host arrays);
+ * types and step index are kept; densities and forces are re-evaluated at the
+ * current step index.  Positions on periodic axes are wrapped into the box. */
+int mdpd_set_state(mdpd_handle* h, const double* pos, const double* vel);
+
+/* Device-array variant of mdpd_set_state. */
+int mdpd_set_state_dev(mdpd_handle* h, const double* pos, const double* vel);
+
+/* Evaluate, without stepping, the density and the forces at the current
+ * positions and velocities with the current step index: force gets 3N doubles
+ * (sum_j F_ij + g for mobile particles, m = 1; 0 for frozen ones), rho N
+ * doubles, id order.  Either pointer may be NULL.  Synchronises. */
+int mdpd_forces(mdpd_handle* h, double* force, double* rho);
+
+/* Device-array variant of mdpd_forces. */
+int mdpd_forces_dev(mdpd_handle* h, double* force, double* rho);
+
+/* Observables of the last force evaluation, reduced in FP64 in a fixed order:
+ * out[0..2] momentum, out[3] kinetic energy, out[4] kT = 2 KE / (3 (N_m - 1)),
+ * out[5..10] conservative virial 1/2 sum_{i mobile} sum_j r_ij,a F^C_ij,b
+ * (xx yy zz xy xz yz), out[11..13] sum v_a^2, out[14] N_m (mobile count),
+ * out[15] step index.  Synchronises. */
+int mdpd_observables(mdpd_handle* h, double out[MDPD_NUM_OBS]);
+
+/* Mean of the per-step observables over the steps since the last reset
+ * (reset != 0 clears the accumulator after reading).  Synchronises. */
+int mdpd_observables_mean(mdpd_handle* h, double out[MDPD_NUM_OBS], int32_t reset);
+
+/* Pair evaluations (0 < r < r_c) of the last force pass: every mobile
+ * particle counts its partners, so a pair of two mobile particles counts
+ * twice.  Synchronises. */
+int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
+
+/* Options (mdpd_set_option):
+ *   MDPD_OPT_GRAPH     1 (default): replay each step as a captured CUDA graph;
+ *                      0: launch kernels one by one.
+ *   MDPD_OPT_PROFILE   k > 0: record CUDA events around every kernel class of
+ *                      the next steps (up to k steps); 0: off.
+ */
+enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2 };
+int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
+
+/* Kernel classes reported by mdpd_profile(). */
+enum { MDPD_K_BIN = 0, MDPD_K_DENSITY = 1, MDPD_K_FORCE = 2, MDPD_K_OTHER = 3,
+       MDPD_NUM_KCLASS = 4 };
+
+/* Sum of the recorded kernel durations per class (ms) and the number of steps
+ * recorded; clears the record.  Synchronises. */
+int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps,
+                 int64_t* launches);
+
+/* Grid of the cell lattice (cells per axis) and the kernel launches one step
+ * issues. */
+int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_step);
+
+void mdpd_destroy(mdpd_handle* h);
+
+/* Message of the last error on h (or of the last failed mdpd_create when h is
+ * NULL).  Valid until the next call on the same handle. */
+const char* mdpd_last_error(const mdpd_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MDPD_H */

@@ -542,3 +542,39 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Forces on a subset of particles (indices idx[0..m-1]) of the whole system,  */
+/* with rho given for every particle; same definition as orc_forces.          */
+int orc_forces_subset(const orc_sys *s, int64_t n, const double *x, const double *v,
+                      const int32_t *type, const uint32_t *id, const double *rho,
+                      uint64_t step, int64_t m, const int64_t *idx, double *a)
+{
+    orc_cells c = { { 0, 0, 0 }, { 0, 0, 0 }, NULL, NULL };
+    if (s->use_cells && cells_build(s, n, x, &c) != 0) { cells_free(&c); return -1; }
+#pragma omp parallel
+    {
+        orc_list lst = { NULL, 0, 0 };
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t q = 0; q < m; ++q) {
+            const int64_t i = idx[q];
+            double F[3] = { 0.0, 0.0, 0.0 };
+            if (!is_frozen(s, type[i])) {
+                candidates(s, &c, n, x, i, &lst);
+                for (int64_t k = 0; k < lst.n; ++k) {
+                    int64_t j = lst.j[k];
+                    double d[3], vij[3], f[3];
+                    pair_vec(s, &x[3 * i], &x[3 * j], d);
+                    for (int r = 0; r < 3; ++r) vij[r] = v[3 * i + r] - v[3 * j + r];
+                    double xi = orc_xi(s->seed, step, id[i], id[j], s->xi_dist);
+                    if (orc_pair_force(s, d, vij, type[i], type[j], rho[i], rho[j], xi, f, NULL))
+                        for (int r = 0; r < 3; ++r) F[r] += f[r];
+                }
+                for (int r = 0; r < 3; ++r) F[r] += s->g[r];
+            }
+            for (int r = 0; r < 3; ++r) a[3 * q + r] = F[r];
+        }
+        free(lst.j);
+    }
+    if (s->use_cells) cells_free(&c);
+    return 0;
+}

@@ -67,6 +67,7 @@ def lib():
         _lib.orc_place_walls.argtypes = [P, P, P, d, P, d, d, u64, P, i64, P]
         _lib.orc_place_walls.restype = i64
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_forces_subset.argtypes = [P, i64, P, P, P, P, P, u64, i64, P, P]
     return _lib
 
 
@@ -211,6 +212,20 @@ class Oracle:
                             _ptr(self.ids), _ptr(rho), int(step), _ptr(a), _ptr(vir)) != 0:
             raise RuntimeError("oracle forces failed")
         return a, vir
+
+    def forces_subset(self, idx, x=None, v=None, rho=None, step=None):
+        """Accelerations of the particles idx (rho of all particles needed)."""
+        x = self.x if x is None else _c(x, np.float64)
+        v = self.v if v is None else _c(v, np.float64)
+        rho = self.density(x) if rho is None else _c(rho, np.float64)
+        step = self.step if step is None else step
+        idx = _c(idx, np.int64)
+        a = np.zeros((idx.shape[0], 3))
+        if lib().orc_forces_subset(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(v),
+                                   _ptr(self.type), _ptr(self.ids), _ptr(rho), int(step),
+                                   idx.shape[0], _ptr(idx), _ptr(a)) != 0:
+            raise RuntimeError("oracle forces failed")
+        return a
 
     def refresh(self):
         """Recompute rho and a(t) of the current state (step index unchanged)."""

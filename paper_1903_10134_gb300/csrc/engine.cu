@@ -1,0 +1,985 @@
+// Host side of the C ABI (include/mdpd.h): owns the device state of one mDPD
+// system, validates arguments, enqueues the kernels of a time step on the
+// handle's stream (directly or as a captured CUDA graph) and moves data in
+// and out in particle-id order.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mdpd_internal.cuh"
+#include "vec.cuh"
+
+using namespace mdpd;
+
+namespace {
+
+constexpr int64_t MAX_PARTICLES = int64_t(1) << 30;
+constexpr int64_t MAX_SCAN = int64_t(4096) * 4096;   // limit of the two-level scan
+constexpr int EV_PER_STEP = 5;                        // profile events per step
+
+std::string g_create_error;
+
+struct Graphs {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_node[EV_PER_STEP] = {};
+};
+
+}  // namespace
+
+struct mdpd_handle {
+    mdpd_params p{};
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint64_t seed = 0;
+    int precision = 1;
+    int64_t n = 0, n_user = 0, cap = 0;
+    Geo geo{};
+    Phys ph{};
+    MaskDev mk{};
+
+    // master state, ping-pong between binnings
+    double* x[2] = {};
+    double* v[2] = {};
+    double* a[2] = {};
+    uint32_t* id[2] = {};
+    uint8_t* type[2] = {};
+    int cur = 0;
+    // cell-ordered compute arrays
+    void* pos4 = nullptr;
+    void* vel4 = nullptr;
+    void* rho = nullptr;
+    uint32_t* cell_s = nullptr;
+    // binning
+    uint32_t *count = nullptr, *start = nullptr, *cellof = nullptr, *slot = nullptr;
+    uint32_t *key = nullptr, *src = nullptr, *scan_tmp = nullptr;
+    // misc
+    uint32_t* status = nullptr;
+    uint64_t* step = nullptr;
+    double* partials = nullptr;
+    double* obs = nullptr;       // MDPD_NUM_OBS current, then MDPD_NUM_OBS sums, then count
+    double* fout = nullptr;      // 3 * cap staging / force output
+    uint8_t* type_by_id = nullptr;
+    uint32_t* mask_bits = nullptr;
+    bool walls_set = false;
+    std::vector<int32_t> h_type;
+    int64_t steps_host = 0;
+
+    // graphs[profiled][mode: 0 fused, 1 last][cur]
+    bool use_graph = true;
+    Graphs g[2][2][2];
+    cudaEvent_t tev[EV_PER_STEP] = {};
+
+    // profiling ring
+    int64_t prof_cap = 0, prof_used = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    int64_t prof_launches = 0;
+
+    std::string err;
+
+    int fail(int code, const std::string& msg)
+    {
+        err = msg;
+        return code;
+    }
+};
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return h->fail(MDPD_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+namespace {
+
+template <typename P>
+int dalloc(mdpd_handle* h, P** ptr, size_t bytes)
+{
+    *ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc((void**)ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *ptr = nullptr;
+        return h->fail(MDPD_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) +
+                                         "): " + cudaGetErrorString(e));
+    }
+    return MDPD_OK;
+}
+
+template <typename P>
+void dfree(P*& ptr)
+{
+    if (ptr) cudaFree((void*)ptr);
+    ptr = nullptr;
+}
+
+Master master(mdpd_handle* h, int k)
+{
+    Master m;
+    m.x = h->x[k];
+    m.v = h->v[k];
+    m.a = h->a[k];
+    m.id = h->id[k];
+    m.type = h->type[k];
+    return m;
+}
+
+void free_particles(mdpd_handle* h)
+{
+    for (int k = 0; k < 2; ++k) {
+        dfree(h->x[k]);
+        dfree(h->v[k]);
+        dfree(h->a[k]);
+        dfree(h->id[k]);
+        dfree(h->type[k]);
+    }
+    dfree(h->pos4);
+    dfree(h->vel4);
+    dfree(h->rho);
+    dfree(h->cell_s);
+    dfree(h->cellof);
+    dfree(h->slot);
+    dfree(h->key);
+    dfree(h->src);
+    dfree(h->partials);
+    dfree(h->fout);
+    dfree(h->type_by_id);
+}
+
+int alloc_particles(mdpd_handle* h, int64_t cap)
+{
+    const size_t c = (size_t)(cap > 0 ? cap : 1);
+    const size_t tsz = h->precision == 0 ? sizeof(double) : sizeof(float);
+    const size_t v4 = h->precision == 0 ? sizeof(D4) : sizeof(float4);
+    int rc = MDPD_OK;
+    for (int k = 0; k < 2 && rc == MDPD_OK; ++k) {
+        if ((rc = dalloc(h, &h->x[k], 3 * c * sizeof(double)))) break;
+        if ((rc = dalloc(h, &h->v[k], 3 * c * sizeof(double)))) break;
+        if ((rc = dalloc(h, &h->a[k], 3 * c * sizeof(double)))) break;
+        if ((rc = dalloc(h, &h->id[k], c * sizeof(uint32_t)))) break;
+        if ((rc = dalloc(h, &h->type[k], c))) break;
+    }
+    if (!rc) rc = dalloc(h, &h->pos4, c * v4);
+    if (!rc) rc = dalloc(h, &h->vel4, c * v4);
+    if (!rc) rc = dalloc(h, &h->rho, c * tsz);
+    if (!rc) rc = dalloc(h, &h->cell_s, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->cellof, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->slot, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->key, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->src, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->partials, (size_t)force_num_blocks((int)c) * OBS_PARTIALS * sizeof(double));
+    if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
+    if (!rc) rc = dalloc(h, &h->type_by_id, c);
+    if (!rc) h->cap = (int64_t)c;
+    return rc;
+}
+
+void destroy_graphs(mdpd_handle* h)
+{
+    for (auto& a : h->g)
+        for (auto& b : a)
+            for (auto& gg : b) {
+                if (gg.exec) cudaGraphExecDestroy(gg.exec);
+                if (gg.graph) cudaGraphDestroy(gg.graph);
+                gg = Graphs();
+            }
+}
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+int validate_params(const mdpd_params* p, std::string& why)
+{
+    if (!p) { why = "params is NULL"; return MDPD_ERR_INVALID_ARG; }
+    if (p->ntypes < 1 || p->ntypes > MDPD_MAX_TYPES) { why = "ntypes must be in 1..8"; return MDPD_ERR_INVALID_ARG; }
+    if (!(p->rc > 0) || !is_fin(p->rc)) { why = "rc must be > 0"; return MDPD_ERR_INVALID_ARG; }
+    if (!(p->rd > 0) || !(p->rd <= p->rc)) { why = "rd must be in (0, rc]"; return MDPD_ERR_INVALID_ARG; }
+    if (!(p->dt > 0) || !is_fin(p->dt)) { why = "dt must be > 0"; return MDPD_ERR_INVALID_ARG; }
+    if (!(p->kT >= 0) || !is_fin(p->kT)) { why = "kT must be >= 0"; return MDPD_ERR_INVALID_ARG; }
+    if (p->precision != 0 && p->precision != 1) { why = "precision must be 0 or 1"; return MDPD_ERR_INVALID_ARG; }
+    if (p->xi_dist != 0 && p->xi_dist != 1) { why = "xi_dist must be 0 or 1"; return MDPD_ERR_INVALID_ARG; }
+    for (int k = 0; k < 3; ++k) {
+        if (!(p->box[k] > 0) || !is_fin(p->box[k]) || !is_fin(p->box_lo[k])) {
+            why = "box lengths must be finite and > 0";
+            return MDPD_ERR_INVALID_ARG;
+        }
+        if (p->periodic[k] && p->box[k] < 3.0 * p->rc) {
+            why = "a periodic axis must be at least 3 rc long";
+            return MDPD_ERR_INVALID_ARG;
+        }
+        if (!is_fin(p->g[k])) { why = "g must be finite"; return MDPD_ERR_INVALID_ARG; }
+    }
+    for (int a = 0; a < MDPD_MAX_TYPES; ++a)
+        for (int b = 0; b < MDPD_MAX_TYPES; ++b) {
+            if (!is_fin(p->A[a][b]) || !is_fin(p->B[a][b]) || !is_fin(p->gamma[a][b]) ||
+                p->gamma[a][b] < 0) {
+                why = "pair tables must be finite with gamma >= 0";
+                return MDPD_ERR_INVALID_ARG;
+            }
+            if (a < p->ntypes && b < p->ntypes &&
+                (p->A[a][b] != p->A[b][a] || p->B[a][b] != p->B[b][a] ||
+                 p->gamma[a][b] != p->gamma[b][a])) {
+                why = "pair tables must be symmetric";
+                return MDPD_ERR_INVALID_ARG;
+            }
+        }
+    return MDPD_OK;
+}
+
+void setup_geo_phys(mdpd_handle* h)
+{
+    const mdpd_params& p = h->p;
+    Geo& g = h->geo;
+    g.ncell = 1;
+    for (int k = 0; k < 3; ++k) {
+        int m = (int)std::floor(p.box[k] / p.rc);
+        if (m < 1) m = 1;
+        g.nc[k] = m;
+        g.periodic[k] = p.periodic[k] ? 1 : 0;
+        g.lo[k] = p.box_lo[k];
+        g.L[k] = p.box[k];
+        g.hi[k] = p.box_lo[k] + p.box[k];
+        g.h[k] = p.box[k] / m;
+        g.inv_h[k] = 1.0 / g.h[k];
+        g.ncell *= m;
+    }
+    Phys& f = h->ph;
+    f.rc = p.rc;
+    f.rd = p.rd;
+    f.dt = p.dt;
+    f.hdt = 0.5 * p.dt;
+    f.kT = p.kT;
+    for (int k = 0; k < 3; ++k) f.g[k] = p.g[k];
+    f.frozen = p.frozen_type_mask & 0xFFu;
+    f.ntypes = p.ntypes;
+    f.xi_dist = p.xi_dist;
+    f.rho_self = p.rho_self ? 1 : 0;
+    f.key0 = (uint32_t)h->seed;
+    f.key1 = (uint32_t)(h->seed >> 32);
+    for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b) {
+            f.A[a * 8 + b] = p.A[a][b];
+            f.B[a * 8 + b] = p.B[a][b];
+            f.gamma[a * 8 + b] = p.gamma[a][b];
+            f.sigma[a * 8 + b] = std::sqrt(2.0 * p.gamma[a][b] * p.kT);
+        }
+}
+
+int status_to_code(uint32_t st)
+{
+    if (st & ST_NONFINITE) return MDPD_ERR_NONFINITE;
+    if (st & ST_OUT_OF_BOX) return MDPD_ERR_OUT_OF_BOX;
+    if (st & ST_OVERFLOW) return MDPD_ERR_TILE_OVERFLOW;
+    if (st & ST_TIMEOUT) return MDPD_ERR_TIMEOUT;
+    return MDPD_OK;
+}
+
+// Synchronise the stream and turn the device status word into an error code
+// (the word is cleared).
+int sync_check(mdpd_handle* h)
+{
+    CK(cudaStreamSynchronize(h->stream));
+    uint32_t st = 0;
+    CK(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
+    if (st) {
+        CK(cudaMemset(h->status, 0, sizeof(uint32_t)));
+        const int code = status_to_code(st);
+        const char* what = code == MDPD_ERR_NONFINITE     ? "non-finite position, velocity or force"
+                           : code == MDPD_ERR_OUT_OF_BOX   ? "a particle left a non-periodic box"
+                           : code == MDPD_ERR_TILE_OVERFLOW ? "cell tile overflow"
+                                                            : "device wait timed out";
+        return h->fail(code, what);
+    }
+    return MDPD_OK;
+}
+
+// ---- one time step, as a sequence of launches ---------------------------------
+
+void record(mdpd_handle* h, cudaEvent_t* evs, int k)
+{
+    if (evs) cudaEventRecord(evs[k], h->stream);
+}
+
+// Bin: count, scan, scatter, per-cell sort, gather into the other buffer.
+void enqueue_bin(mdpd_handle* h, bool gather_a)
+{
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    cudaMemsetAsync(h->count, 0, (size_t)h->geo.ncell * sizeof(uint32_t), st);
+    launch_bin_count(st, n, h->cap, h->x[h->cur], h->geo, h->cellof, h->slot, h->count, h->status);
+    launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp);
+    launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src);
+    launch_cell_sort(st, h->geo.ncell, h->start, h->key, h->src);
+    launch_gather(st, h->precision, n, h->cap, h->src, h->cellof, master(h, h->cur),
+                  master(h, 1 - h->cur), gather_a, h->geo, h->pos4, h->vel4, h->cell_s);
+    h->cur = 1 - h->cur;
+}
+
+void enqueue_density(mdpd_handle* h)
+{
+    launch_density(h->stream, h->precision, (int)h->n, h->geo, h->ph, h->pos4, h->cell_s,
+                   h->start, h->rho);
+}
+
+void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
+{
+    launch_force(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk, h->pos4,
+                 h->vel4, h->rho, h->cell_s, h->start, h->step, step_offset, master(h, h->cur),
+                 out, h->partials, h->status);
+}
+
+void enqueue_reduce(mdpd_handle* h, int advance)
+{
+    launch_reduce_obs(h->stream, h->partials, force_num_blocks((int)h->n), h->obs,
+                      h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS, h->step, advance, 0.0);
+}
+
+// One velocity-Verlet step after the first half-kick and drift:
+// bin, density, force (+ half-kick [+ next half-kick, drift]), reduction.
+void enqueue_step(mdpd_handle* h, ForceMode mode, cudaEvent_t* evs)
+{
+    record(h, evs, 0);
+    enqueue_bin(h, false);
+    record(h, evs, 1);
+    enqueue_density(h);
+    record(h, evs, 2);
+    enqueue_force(h, mode, 1, nullptr);
+    record(h, evs, 3);
+    enqueue_reduce(h, 1);
+    record(h, evs, 4);
+}
+
+constexpr int LAUNCHES_PER_STEP = 10;
+
+// Density and forces at the current state (no integration); the result goes
+// to `out` (3 * cap doubles, cell order) or, if out is NULL, to the
+// integration acceleration a.
+int evaluate(mdpd_handle* h, double* out, bool keep_a)
+{
+    enqueue_bin(h, keep_a);
+    enqueue_density(h);
+    enqueue_force(h, FM_EVAL, 0, out ? out : h->a[h->cur]);
+    enqueue_reduce(h, 0);
+    CK(cudaGetLastError());
+    return MDPD_OK;
+}
+
+int capture_step(mdpd_handle* h, int prof, int mode, int cur)
+{
+    Graphs& gg = h->g[prof][mode][cur];
+    const int saved = h->cur;
+    h->cur = cur;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(h, mode == 0 ? FM_FUSED : FM_LAST, prof ? h->tev : nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->cur = saved;
+    if (e != cudaSuccess) return h->fail(MDPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return h->fail(MDPD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    gg.graph = graph;
+    gg.exec = exec;
+    if (prof) {
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
+        for (auto nd : nodes) {
+            cudaGraphNodeType t;
+            CK(cudaGraphNodeGetType(nd, &t));
+            if (t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            for (int k = 0; k < EV_PER_STEP; ++k)
+                if (ev == h->tev[k]) gg.ev_node[k] = nd;
+        }
+    }
+    return MDPD_OK;
+}
+
+cudaEvent_t* next_prof_events(mdpd_handle* h)
+{
+    if (h->prof_used >= h->prof_cap) return nullptr;
+    cudaEvent_t* evs = &h->prof_ev[(size_t)h->prof_used * EV_PER_STEP];
+    ++h->prof_used;
+    return evs;
+}
+
+int run_step(mdpd_handle* h, ForceMode mode)
+{
+    cudaEvent_t* evs = next_prof_events(h);
+    h->prof_launches += LAUNCHES_PER_STEP;
+    if (!h->use_graph) {
+        enqueue_step(h, mode, evs);
+        CK(cudaGetLastError());
+        return MDPD_OK;
+    }
+    const int prof = evs ? 1 : 0;
+    const int mi = mode == FM_FUSED ? 0 : 1;
+    Graphs& gg = h->g[prof][mi][h->cur];
+    if (!gg.exec) {
+        int rc = capture_step(h, prof, mi, h->cur);
+        if (rc) return rc;
+    }
+    if (prof)
+        for (int k = 0; k < EV_PER_STEP; ++k)
+            CK(cudaGraphExecEventRecordNodeSetEvent(gg.exec, gg.ev_node[k], evs[k]));
+    CK(cudaGraphLaunch(gg.exec, h->stream));
+    h->cur = 1 - h->cur;
+    return MDPD_OK;
+}
+
+int check_ptr_kind(mdpd_handle* h, const void* p, bool want_device)
+{
+    if (!p) return MDPD_OK;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return want_device ? h->fail(MDPD_ERR_INVALID_ARG, "pointer is not a device pointer") : MDPD_OK;
+    }
+    if (want_device && at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return h->fail(MDPD_ERR_INVALID_ARG, "pointer is not a device pointer");
+    return MDPD_OK;
+}
+
+int create_common(const mdpd_params* params, int64_t n, const double* pos, const double* vel,
+                  const int32_t* type, uint64_t seed, void* stream, mdpd_handle** out,
+                  bool device_inputs)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return MDPD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    std::string why;
+    int rc = validate_params(params, why);
+    if (rc) { g_create_error = why; return rc; }
+    if (n < 0 || n > MAX_PARTICLES) { g_create_error = "n out of range"; return MDPD_ERR_INVALID_ARG; }
+    if (n > 0 && (!pos || !vel || !type)) { g_create_error = "pos, vel and type are required"; return MDPD_ERR_INVALID_ARG; }
+    if (!device_inputs)
+        for (int64_t i = 0; i < n; ++i)
+            if (type[i] < 0 || type[i] >= params->ntypes) {
+                g_create_error = "type out of range at particle " + std::to_string(i);
+                return MDPD_ERR_INVALID_ARG;
+            }
+
+    mdpd_handle* h = new mdpd_handle();
+    h->p = *params;
+    h->seed = seed;
+    h->precision = params->precision;
+    h->n = h->n_user = n;
+    setup_geo_phys(h);
+    auto bail = [&](int code) {
+        g_create_error = h->err;
+        mdpd_destroy(h);
+        return code;
+    };
+    if (h->geo.ncell > MAX_SCAN) {
+        h->err = "too many cells (box / rc exceeds 16.7M cells)";
+        return bail(MDPD_ERR_INVALID_ARG);
+    }
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        h->err = "no CUDA device";
+        return bail(MDPD_ERR_CUDA);
+    }
+    if (stream) {
+        h->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            h->err = "cudaStreamCreate failed";
+            return bail(MDPD_ERR_CUDA);
+        }
+        h->own_stream = true;
+    }
+    if (device_inputs) {
+        if ((rc = check_ptr_kind(h, pos, true)) || (rc = check_ptr_kind(h, vel, true)) ||
+            (rc = check_ptr_kind(h, type, true)))
+            return bail(rc);
+    }
+
+    // types: validated on the host
+    h->h_type.assign((size_t)n, 0);
+    if (n > 0) {
+        if (device_inputs) {
+            if (cudaMemcpy(h->h_type.data(), type, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                h->err = "copy of types failed";
+                return bail(MDPD_ERR_CUDA);
+            }
+        } else {
+            std::memcpy(h->h_type.data(), type, (size_t)n * sizeof(int32_t));
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (h->h_type[i] < 0 || h->h_type[i] >= params->ntypes) {
+                h->err = "type out of range at particle " + std::to_string(i);
+                return bail(MDPD_ERR_INVALID_ARG);
+            }
+    }
+    if ((rc = alloc_particles(h, n))) return bail(rc);
+    const int64_t nb = scan_num_blocks(h->geo.ncell);
+    if ((rc = dalloc(h, &h->count, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->start, (size_t)(h->geo.ncell + 1) * sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->scan_tmp, (size_t)(nb + 1) * sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->status, sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->step, sizeof(uint64_t))) ||
+        (rc = dalloc(h, &h->obs, (2 * MDPD_NUM_OBS + 2) * sizeof(double))))
+        return bail(rc);
+    for (int k = 0; k < EV_PER_STEP; ++k)
+        if (cudaEventCreate(&h->tev[k]) != cudaSuccess) {
+            h->err = "cudaEventCreate failed";
+            return bail(MDPD_ERR_CUDA);
+        }
+
+    // upload: positions to fout, velocities to x[1] (both 3n staging), types
+    std::vector<uint8_t> t8((size_t)n);
+    for (int64_t i = 0; i < n; ++i) t8[i] = (uint8_t)h->h_type[i];
+    cudaStream_t st = h->stream;
+    const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    bool ok = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), st) == cudaSuccess &&
+              cudaMemsetAsync(h->step, 0, sizeof(uint64_t), st) == cudaSuccess &&
+              cudaMemsetAsync(h->obs, 0, (2 * MDPD_NUM_OBS + 2) * sizeof(double), st) == cudaSuccess;
+    if (ok && n > 0)
+        ok = cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), kind, st) == cudaSuccess &&
+             cudaMemcpyAsync(h->x[1], vel, (size_t)n * 3 * sizeof(double), kind, st) == cudaSuccess &&
+             cudaMemcpyAsync(h->type_by_id, t8.data(), (size_t)n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (!ok) {
+        h->err = "initial upload failed";
+        return bail(MDPD_ERR_CUDA);
+    }
+    h->cur = 0;
+    launch_load_state(st, (int)n, h->cap, h->fout, h->x[1], h->geo, master(h, 0), h->type_by_id,
+                      h->status);
+    if ((rc = evaluate(h, nullptr, false))) return bail(rc);
+    if ((rc = sync_check(h))) return bail(rc);
+    *out = h;
+    return MDPD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mdpd_create(const mdpd_params* params, int64_t n, const double* pos, const double* vel,
+                const int32_t* type, uint64_t seed, void* cuda_stream, mdpd_handle** out)
+{
+    return create_common(params, n, pos, vel, type, seed, cuda_stream, out, false);
+}
+
+int mdpd_create_dev(const mdpd_params* params, int64_t n, const double* pos, const double* vel,
+                    const int32_t* type, uint64_t seed, void* cuda_stream, mdpd_handle** out)
+{
+    return create_common(params, n, pos, vel, type, seed, cuda_stream, out, true);
+}
+
+int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny, int32_t nz,
+                   double voxel, const double origin[3], double wall_density,
+                   double shell_thickness, int32_t wall_type, uint64_t seed)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (h->walls_set) return h->fail(MDPD_ERR_INVALID_ARG, "walls already set");
+    if (!solid || !origin || nx <= 0 || ny <= 0 || nz <= 0 || !(voxel > 0) || !is_fin(voxel))
+        return h->fail(MDPD_ERR_INVALID_ARG, "bad mask dimensions or voxel size");
+    if (wall_type < 0 || wall_type >= h->p.ntypes)
+        return h->fail(MDPD_ERR_INVALID_ARG, "wall_type out of range");
+    if (!(wall_density >= 0) || !is_fin(wall_density) || !(shell_thickness >= 0) || !is_fin(shell_thickness))
+        return h->fail(MDPD_ERR_INVALID_ARG, "wall_density and shell_thickness must be >= 0");
+    const int dim[3] = { nx, ny, nz };
+    const int64_t nvox = (int64_t)nx * ny * nz;
+    if (nvox > MAX_SCAN) return h->fail(MDPD_ERR_INVALID_ARG, "mask larger than 16.7M voxels");
+    for (int k = 0; k < 3; ++k) {
+        if (!h->p.periodic[k]) continue;
+        const double span = dim[k] * voxel;
+        if (std::fabs(span - h->p.box[k]) > 1e-9 * h->p.box[k] ||
+            std::fabs(origin[k] - h->p.box_lo[k]) > 1e-9 * (1.0 + std::fabs(h->p.box_lo[k])))
+            return h->fail(MDPD_ERR_INVALID_ARG, "on a periodic axis the mask must span the box exactly");
+    }
+    int per[3];
+    for (int k = 0; k < 3; ++k) per[k] = h->p.periodic[k] ? 1 : 0;
+    cudaStream_t st = h->stream;
+    int rc;
+    uint8_t* dmask = nullptr;
+    uint32_t *cnt = nullptr, *off = nullptr, *tmp = nullptr;
+    auto cleanup = [&]() {
+        dfree(dmask);
+        dfree(cnt);
+        dfree(off);
+        dfree(tmp);
+    };
+    if ((rc = dalloc(h, &dmask, (size_t)nvox)) || (rc = dalloc(h, &cnt, (size_t)nvox * 4)) ||
+        (rc = dalloc(h, &off, (size_t)(nvox + 1) * 4)) ||
+        (rc = dalloc(h, &tmp, (size_t)(scan_num_blocks(nvox) + 1) * 4))) {
+        cleanup();
+        return rc;
+    }
+    uint32_t* bits = nullptr;
+    if ((rc = dalloc(h, &bits, (size_t)((nvox + 31) / 32) * 4))) {
+        cleanup();
+        return rc;
+    }
+    const double rr = shell_thickness / voxel;
+    const int R = (int)std::floor(rr + 1e-9);
+    const int64_t R2 = (int64_t)std::floor(rr * rr + 1e-9);
+    const double lam = wall_density * voxel * voxel * voxel;
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    uint32_t nw = 0;
+    bool ok = cudaMemcpyAsync(dmask, solid, (size_t)nvox, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    if (ok) {
+        launch_mask_pack(st, dmask, nvox, bits);
+        launch_wall_count(st, dmask, dim, per, R, R2, lam, k0, k1, cnt);
+        launch_exclusive_scan(st, cnt, nvox, off, tmp);
+        ok = cudaMemcpyAsync(&nw, off + nvox, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+             cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    if (!ok) {
+        cleanup();
+        dfree(bits);
+        return h->fail(MDPD_ERR_CUDA, "wall sweep failed");
+    }
+    const int64_t n_old = h->n, n_new = h->n + (int64_t)nw;
+    if (n_new > MAX_PARTICLES) {
+        cleanup();
+        dfree(bits);
+        return h->fail(MDPD_ERR_INVALID_ARG, "too many particles with walls");
+    }
+    // move the state into arrays of the new capacity
+    mdpd_handle tmpH;       // holds the old arrays while the new ones are filled
+    tmpH.precision = h->precision;
+    for (int k = 0; k < 2; ++k) {
+        tmpH.x[k] = h->x[k]; tmpH.v[k] = h->v[k]; tmpH.a[k] = h->a[k];
+        tmpH.id[k] = h->id[k]; tmpH.type[k] = h->type[k];
+        h->x[k] = h->v[k] = h->a[k] = nullptr; h->id[k] = nullptr; h->type[k] = nullptr;
+    }
+    tmpH.pos4 = h->pos4; tmpH.vel4 = h->vel4; tmpH.rho = h->rho; tmpH.cell_s = h->cell_s;
+    tmpH.cellof = h->cellof; tmpH.slot = h->slot; tmpH.key = h->key; tmpH.src = h->src;
+    tmpH.partials = h->partials; tmpH.fout = h->fout; tmpH.type_by_id = h->type_by_id;
+    h->pos4 = h->vel4 = h->rho = nullptr;
+    h->cell_s = h->cellof = h->slot = h->key = h->src = nullptr;
+    h->partials = h->fout = nullptr;
+    h->type_by_id = nullptr;
+    const int64_t old_cap = h->cap;
+    if ((rc = alloc_particles(h, n_new))) {
+        free_particles(h);
+        // restore the old arrays
+        for (int k = 0; k < 2; ++k) {
+            h->x[k] = tmpH.x[k]; h->v[k] = tmpH.v[k]; h->a[k] = tmpH.a[k];
+            h->id[k] = tmpH.id[k]; h->type[k] = tmpH.type[k];
+            tmpH.x[k] = tmpH.v[k] = tmpH.a[k] = nullptr; tmpH.id[k] = nullptr; tmpH.type[k] = nullptr;
+        }
+        h->pos4 = tmpH.pos4; h->vel4 = tmpH.vel4; h->rho = tmpH.rho; h->cell_s = tmpH.cell_s;
+        h->cellof = tmpH.cellof; h->slot = tmpH.slot; h->key = tmpH.key; h->src = tmpH.src;
+        h->partials = tmpH.partials; h->fout = tmpH.fout; h->type_by_id = tmpH.type_by_id;
+        tmpH.pos4 = tmpH.vel4 = tmpH.rho = nullptr;
+        tmpH.cell_s = tmpH.cellof = tmpH.slot = tmpH.key = tmpH.src = nullptr;
+        tmpH.partials = tmpH.fout = nullptr; tmpH.type_by_id = nullptr;
+        h->cap = old_cap;
+        cleanup();
+        dfree(bits);
+        return rc;
+    }
+    const int c = h->cur;
+    ok = true;
+    for (int k = 0; k < 3 && ok; ++k) {
+        ok = cudaMemcpyAsync(h->x[0] + k * h->cap, tmpH.x[c] + k * old_cap, n_old * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+             cudaMemcpyAsync(h->v[0] + k * h->cap, tmpH.v[c] + k * old_cap, n_old * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+             cudaMemcpyAsync(h->a[0] + k * h->cap, tmpH.a[c] + k * old_cap, n_old * sizeof(double), cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+    }
+    ok = ok && cudaMemcpyAsync(h->id[0], tmpH.id[c], n_old * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(h->type[0], tmpH.type[c], (size_t)n_old, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+         cudaMemcpyAsync(h->type_by_id, tmpH.type_by_id, (size_t)n_old, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
+         cudaMemsetAsync(h->type_by_id + n_old, wall_type, (size_t)nw, st) == cudaSuccess;
+    h->cur = 0;
+    if (ok) {
+        launch_wall_emit(st, dmask, dim, cnt, off, voxel, origin, k0, k1, n_old, h->cap,
+                         master(h, 0), (uint8_t)wall_type);
+        ok = cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    free_particles(&tmpH);
+    cleanup();
+    if (!ok) {
+        dfree(bits);
+        return h->fail(MDPD_ERR_CUDA, "wall emission failed");
+    }
+    h->n = n_new;
+    h->h_type.resize((size_t)n_new, wall_type);
+    dfree(h->mask_bits);
+    h->mask_bits = bits;
+    h->mk.bits = bits;
+    for (int k = 0; k < 3; ++k) {
+        h->mk.dim[k] = dim[k];
+        h->mk.origin[k] = origin[k];
+    }
+    h->mk.voxel = voxel;
+    h->walls_set = true;
+    destroy_graphs(h);
+    if ((rc = evaluate(h, nullptr, false))) return rc;
+    return sync_check(h);
+}
+
+int mdpd_step(mdpd_handle* h, int64_t nsteps)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
+    if (nsteps == 0) return MDPD_OK;
+    launch_kick_drift(h->stream, (int)h->n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur),
+                      h->status);
+    h->prof_launches += 1;
+    CK(cudaGetLastError());
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int rc = run_step(h, k + 1 < nsteps ? FM_FUSED : FM_LAST);
+        if (rc) return rc;
+    }
+    h->steps_host += nsteps;
+    return MDPD_OK;
+}
+
+int mdpd_sync(mdpd_handle* h)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    return sync_check(h);
+}
+
+int mdpd_num_particles(const mdpd_handle* h, int64_t* n)
+{
+    if (!h || !n) return MDPD_ERR_INVALID_ARG;
+    *n = h->n;
+    return MDPD_OK;
+}
+
+int mdpd_step_count(const mdpd_handle* h, int64_t* steps)
+{
+    if (!h || !steps) return MDPD_ERR_INVALID_ARG;
+    *steps = h->steps_host;
+    return MDPD_OK;
+}
+
+static int get_state_impl(mdpd_handle* h, double* pos, double* vel, int32_t* type, double* rho,
+                          bool dev)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    const int c = h->cur;
+    double* s_pos = h->fout;
+    double* s_vel = h->x[1 - c];
+    double* s_rho = h->v[1 - c];
+    int32_t* s_type = (int32_t*)h->a[1 - c];
+    if (dev) {
+        s_pos = pos;
+        s_vel = vel;
+        s_rho = rho;
+        s_type = type;
+    }
+    if (pos) launch_scatter_by_id(st, n, h->cap, h->id[c], h->x[c], s_pos);
+    if (vel) launch_scatter_by_id(st, n, h->cap, h->id[c], h->v[c], s_vel);
+    if (rho) launch_scatter_scalar_by_id(st, h->precision, n, h->id[c], h->rho, s_rho);
+    if (type) launch_scatter_type_by_id(st, n, h->id[c], h->type[c], s_type);
+    CK(cudaGetLastError());
+    if (!dev) {
+        if (pos) CK(cudaMemcpyAsync(pos, s_pos, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (vel) CK(cudaMemcpyAsync(vel, s_vel, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (rho) CK(cudaMemcpyAsync(rho, s_rho, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (type) CK(cudaMemcpyAsync(type, s_type, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    return sync_check(h);
+}
+
+int mdpd_get_state(mdpd_handle* h, double* pos, double* vel, int32_t* type, double* rho)
+{
+    return get_state_impl(h, pos, vel, type, rho, false);
+}
+
+int mdpd_get_state_dev(mdpd_handle* h, double* pos, double* vel, int32_t* type, double* rho)
+{
+    if (h) {
+        int rc;
+        if ((rc = check_ptr_kind(h, pos, true)) || (rc = check_ptr_kind(h, vel, true)) ||
+            (rc = check_ptr_kind(h, type, true)) || (rc = check_ptr_kind(h, rho, true)))
+            return rc;
+    }
+    return get_state_impl(h, pos, vel, type, rho, true);
+}
+
+static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, bool dev)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (h->n > 0 && (!pos || !vel)) return h->fail(MDPD_ERR_INVALID_ARG, "pos and vel are required");
+    int rc = sync_check(h);
+    if (rc) return rc;
+    if (dev && ((rc = check_ptr_kind(h, pos, true)) || (rc = check_ptr_kind(h, vel, true)))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    const int c = h->cur;
+    const double* d_pos = pos;
+    const double* d_vel = vel;
+    if (!dev && n > 0) {
+        CK(cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(h->x[1 - c], vel, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+        d_pos = h->fout;
+        d_vel = h->x[1 - c];
+    }
+    launch_load_state(st, n, h->cap, d_pos, d_vel, h->geo, master(h, c), h->type_by_id, h->status);
+    if ((rc = evaluate(h, nullptr, false))) return rc;
+    return MDPD_OK;
+}
+
+int mdpd_set_state(mdpd_handle* h, const double* pos, const double* vel)
+{
+    int rc = set_state_impl(h, pos, vel, false);
+    if (rc) return rc;
+    return MDPD_OK;
+}
+
+int mdpd_set_state_dev(mdpd_handle* h, const double* pos, const double* vel)
+{
+    return set_state_impl(h, pos, vel, true);
+}
+
+static int forces_impl(mdpd_handle* h, double* force, double* rho, bool dev)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    if (dev && ((rc = check_ptr_kind(h, force, true)) || (rc = check_ptr_kind(h, rho, true)))) return rc;
+    if ((rc = evaluate(h, h->fout, true))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    const int c = h->cur;
+    double* s_f = dev ? force : h->x[1 - c];
+    double* s_rho = dev ? rho : h->v[1 - c];
+    if (force) launch_scatter_by_id(st, n, h->cap, h->id[c], h->fout, s_f);
+    if (rho) launch_scatter_scalar_by_id(st, h->precision, n, h->id[c], h->rho, s_rho);
+    CK(cudaGetLastError());
+    if (!dev) {
+        if (force) CK(cudaMemcpyAsync(force, s_f, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        if (rho) CK(cudaMemcpyAsync(rho, s_rho, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
+    return sync_check(h);
+}
+
+int mdpd_forces(mdpd_handle* h, double* force, double* rho) { return forces_impl(h, force, rho, false); }
+
+int mdpd_forces_dev(mdpd_handle* h, double* force, double* rho) { return forces_impl(h, force, rho, true); }
+
+int mdpd_observables(mdpd_handle* h, double out[MDPD_NUM_OBS])
+{
+    if (!h || !out) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(out, h->obs, MDPD_NUM_OBS * sizeof(double), cudaMemcpyDeviceToHost));
+    return MDPD_OK;
+}
+
+int mdpd_observables_mean(mdpd_handle* h, double out[MDPD_NUM_OBS], int32_t reset)
+{
+    if (!h || !out) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    double buf[MDPD_NUM_OBS + 1];
+    CK(cudaMemcpy(buf, h->obs + MDPD_NUM_OBS, (MDPD_NUM_OBS + 1) * sizeof(double), cudaMemcpyDeviceToHost));
+    const double cnt = buf[MDPD_NUM_OBS];
+    for (int k = 0; k < MDPD_NUM_OBS; ++k) out[k] = cnt > 0 ? buf[k] / cnt : 0.0;
+    if (reset) CK(cudaMemset(h->obs + MDPD_NUM_OBS, 0, (MDPD_NUM_OBS + 1) * sizeof(double)));
+    return MDPD_OK;
+}
+
+int mdpd_pair_count(mdpd_handle* h, int64_t* pairs)
+{
+    if (!h || !pairs) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    double v = 0.0;
+    CK(cudaMemcpy(&v, h->obs + 2 * MDPD_NUM_OBS + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    *pairs = (int64_t)v;
+    return MDPD_OK;
+}
+
+int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    switch (option) {
+    case MDPD_OPT_GRAPH:
+        h->use_graph = value != 0;
+        return MDPD_OK;
+    case MDPD_OPT_PROFILE: {
+        if (value < 0 || value > (int64_t(1) << 20)) return h->fail(MDPD_ERR_INVALID_ARG, "profile steps out of range");
+        CK(cudaStreamSynchronize(h->stream));
+        const size_t need = (size_t)value * EV_PER_STEP;
+        while (h->prof_ev.size() < need) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->prof_ev.push_back(e);
+        }
+        h->prof_cap = value;
+        h->prof_used = 0;
+        h->prof_launches = 0;
+        return MDPD_OK;
+    }
+    default:
+        return h->fail(MDPD_ERR_INVALID_ARG, "unknown option");
+    }
+}
+
+int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps, int64_t* launches)
+{
+    if (!h || !ms) return MDPD_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < MDPD_NUM_KCLASS; ++k) ms[k] = 0.0;
+    for (int64_t s = 0; s < h->prof_used; ++s) {
+        cudaEvent_t* e = &h->prof_ev[(size_t)s * EV_PER_STEP];
+        for (int k = 0; k < MDPD_NUM_KCLASS; ++k) {
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, e[k], e[k + 1]));
+            ms[k] += t;
+        }
+    }
+    if (steps) *steps = h->prof_used;
+    if (launches) *launches = h->prof_launches;
+    h->prof_used = 0;
+    h->prof_launches = 0;
+    return MDPD_OK;
+}
+
+int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_step)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (ncell)
+        for (int k = 0; k < 3; ++k) ncell[k] = h->geo.nc[k];
+    if (launches_per_step) *launches_per_step = LAUNCHES_PER_STEP;
+    return MDPD_OK;
+}
+
+void mdpd_destroy(mdpd_handle* h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    destroy_graphs(h);
+    free_particles(h);
+    dfree(h->count);
+    dfree(h->start);
+    dfree(h->scan_tmp);
+    dfree(h->status);
+    dfree(h->step);
+    dfree(h->obs);
+    dfree(h->mask_bits);
+    for (auto& e : h->tev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : h->prof_ev) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+const char* mdpd_last_error(const mdpd_handle* h)
+{
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+}  // extern "C"

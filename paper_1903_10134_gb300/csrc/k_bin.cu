@@ -1,0 +1,336 @@
+// Cell binning by a stable counting sort (per step): cell id of every
+// particle, per-cell counts, exclusive scan, scatter, a per-cell sort of the
+// slots by particle id (so the order inside a cell does not depend on the
+// order of the atomics), and a gather of the state into cell order with
+// positions re-expressed as offsets from the cell centre.
+#include "mdpd_internal.cuh"
+#include "vec.cuh"
+
+namespace mdpd {
+
+namespace {
+
+constexpr int BLOCK = 256;
+
+inline unsigned nblocks(int64_t n, int b = BLOCK) { return (unsigned)((n + b - 1) / b); }
+
+__global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Geo geo,
+                            uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
+                            uint32_t* __restrict__ count, uint32_t* __restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int q[3];
+    uint32_t st = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const double xk = x[k * cap + i];
+        if (!isfinite(xk)) {
+            st |= ST_NONFINITE;
+            q[k] = 0;
+            continue;
+        }
+        if (!geo.periodic[k] && (xk < geo.lo[k] || xk >= geo.hi[k])) st |= ST_OUT_OF_BOX;
+        int c = (int)floor((xk - geo.lo[k]) * geo.inv_h[k]);
+        c = c < 0 ? 0 : (c >= geo.nc[k] ? geo.nc[k] - 1 : c);
+        q[k] = c;
+    }
+    if (st) atomicOr(status, st);
+    const uint32_t c = (uint32_t)(q[0] + geo.nc[0] * (q[1] + geo.nc[1] * q[2]));
+    cellof[i] = c;
+    slot[i] = atomicAdd(&count[c], 1u);
+}
+
+// ---- exclusive scan ------------------------------------------------------------
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// Exclusive prefix of v over the block; *total receives the block sum.
+__device__ uint32_t block_exclusive(uint32_t v, uint32_t* total)
+{
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarp = blockDim.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nwarp ? wsum[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t base = warp > 0 ? wsum[warp - 1] : 0u;
+    *total = wsum[nwarp - 1];
+    __syncthreads();
+    return base + incl - v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const uint32_t* __restrict__ in,
+                                                              int64_t n, uint32_t* __restrict__ sums)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k)
+        if (base + k < n) s += in[base + k];
+    uint32_t total;
+    block_exclusive(s, &total);
+    if (threadIdx.x == 0) sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the nb block sums in place; sums[nb] = total.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(uint32_t* __restrict__ sums, int nb)
+{
+    const int base = threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < nb ? sums[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive(s, &total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < nb) sums[base + k] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) sums[nb] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __restrict__ in,
+                                                             int64_t n,
+                                                             const uint32_t* __restrict__ sums,
+                                                             int nb, uint32_t* __restrict__ out)
+{
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_exclusive(s, &total) + sums[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = run;
+        run += v[k];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nb];
+}
+
+__global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
+                              const uint32_t* __restrict__ slot, const uint32_t* __restrict__ start,
+                              const uint32_t* __restrict__ id, uint32_t* __restrict__ key,
+                              uint32_t* __restrict__ src)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t dst = start[cellof[i]] + slot[i];
+    key[dst] = id[i];
+    src[dst] = (uint32_t)i;
+}
+
+// Insertion sort of each cell's slots by particle id.
+__global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ src)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncell) return;
+    const uint32_t b = start[c], e = start[c + 1];
+    for (uint32_t a = b + 1; a < e; ++a) {
+        const uint32_t k = key[a], s = src[a];
+        uint32_t p = a;
+        while (p > b && key[p - 1] > k) {
+            key[p] = key[p - 1];
+            src[p] = src[p - 1];
+            --p;
+        }
+        key[p] = k;
+        src[p] = s;
+    }
+}
+
+template <typename T>
+__global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
+                         const uint32_t* __restrict__ cellof, Master in, Master out,
+                         int gather_a, Geo geo, typename Vec4<T>::type* __restrict__ pos4,
+                         typename Vec4<T>::type* __restrict__ vel4, uint32_t* __restrict__ cell_s)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t i = src[s];
+    const uint32_t c = cellof[i];
+    const int q[3] = { (int)(c % (uint32_t)geo.nc[0]),
+                       (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]),
+                       (int)(c / ((uint32_t)geo.nc[0] * (uint32_t)geo.nc[1])) };
+    double xv[3], vv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xv[k] = in.x[k * cap + i];
+        vv[k] = in.v[k * cap + i];
+        out.x[k * cap + s] = xv[k];
+        out.v[k * cap + s] = vv[k];
+        if (gather_a) out.a[k * cap + s] = in.a[k * cap + i];
+    }
+    const uint32_t pid = in.id[i];
+    const uint8_t pt = in.type[i];
+    out.id[s] = pid;
+    out.type[s] = pt;
+    cell_s[s] = c;
+    T off[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        off[k] = (T)(xv[k] - geo.lo[k] - ((double)q[k] + 0.5) * geo.h[k]);
+    pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
+    vel4[s] = make4((T)vv[0], (T)vv[1], (T)vv[2], pack_u32(T(0), pid));
+}
+
+// Load a state given in id order (pos/vel interleaved xyz) into the master
+// arrays (index = id), wrapping periodic axes.
+__global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3,
+                             const double* __restrict__ vel3, Geo geo, Master m,
+                             const uint8_t* __restrict__ type_by_id, uint32_t* __restrict__ status)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t st = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double x = pos3[3 * i + k];
+        const double v = vel3[3 * i + k];
+        if (!isfinite(x) || !isfinite(v)) st |= ST_NONFINITE;
+        if (geo.periodic[k] && isfinite(x)) {
+            const double w = floor((x - geo.lo[k]) / geo.L[k]);
+            if (w != 0.0) x -= geo.L[k] * w;      // in-box positions stay bit-identical
+            if (x >= geo.hi[k] || x < geo.lo[k]) x = geo.lo[k];
+        }
+        m.x[k * cap + i] = x;
+        m.v[k * cap + i] = v;
+        m.a[k * cap + i] = 0.0;
+    }
+    if (st) atomicOr(status, st);
+    m.id[i] = (uint32_t)i;
+    m.type[i] = type_by_id[i];
+}
+
+__global__ void k_scatter_vec_by_id(int n, int64_t cap, const uint32_t* __restrict__ id,
+                                    const double* __restrict__ v, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const uint32_t d = id[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[3 * (int64_t)d + k] = v[k * cap + s];
+}
+
+template <typename T>
+__global__ void k_scatter_scalar_by_id(int n, const uint32_t* __restrict__ id,
+                                       const T* __restrict__ r, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    out[id[s]] = (double)r[s];
+}
+
+__global__ void k_scatter_type_by_id(int n, const uint32_t* __restrict__ id,
+                                     const uint8_t* __restrict__ t, int32_t* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    out[id[s]] = (int32_t)t[s];
+}
+
+}  // namespace
+
+void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, const Geo& geo,
+                      uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
+{
+    if (n <= 0) return;
+    k_bin_count<<<nblocks(n), BLOCK, 0, st>>>(n, cap, x, geo, cellof, slot, count, status);
+}
+
+int scan_num_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
+
+void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint32_t* out,
+                           uint32_t* tmp)
+{
+    const int nb = scan_num_blocks(n);
+    if (nb <= 0) return;
+    k_scan_blocks<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp);
+    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(tmp, nb);
+    k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp, nb, out);
+}
+
+void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
+                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src)
+{
+    if (n <= 0) return;
+    k_bin_scatter<<<nblocks(n), BLOCK, 0, st>>>(n, cellof, slot, start, id, key, src);
+}
+
+void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
+                      uint32_t* src)
+{
+    if (ncell <= 0) return;
+    k_cell_sort<<<nblocks(ncell), BLOCK, 0, st>>>(ncell, start, key, src);
+}
+
+void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
+                   const uint32_t* cellof, const Master& in, const Master& out, bool gather_a,
+                   const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s)
+{
+    if (n <= 0) return;
+    if (precision == 0)
+        k_gather<double><<<nblocks(n), BLOCK, 0, st>>>(n, cap, src, cellof, in, out, gather_a,
+                                                       geo, (D4*)pos4, (D4*)vel4, cell_s);
+    else
+        k_gather<float><<<nblocks(n), BLOCK, 0, st>>>(n, cap, src, cellof, in, out, gather_a,
+                                                      geo, (float4*)pos4, (float4*)vel4, cell_s);
+}
+
+void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
+                       const double* vel3, const Geo& geo, const Master& m,
+                       const uint8_t* type_by_id, uint32_t* status)
+{
+    if (n <= 0) return;
+    k_load_state<<<nblocks(n), BLOCK, 0, st>>>(n, cap, pos3, vel3, geo, m, type_by_id, status);
+}
+
+void launch_scatter_by_id(cudaStream_t st, int n, int64_t cap, const uint32_t* id,
+                          const double* vec3, double* out3)
+{
+    if (n <= 0) return;
+    k_scatter_vec_by_id<<<nblocks(n), BLOCK, 0, st>>>(n, cap, id, vec3, out3);
+}
+
+void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const uint32_t* id,
+                                 const void* r, double* out)
+{
+    if (n <= 0) return;
+    if (precision == 0)
+        k_scatter_scalar_by_id<double><<<nblocks(n), BLOCK, 0, st>>>(n, id, (const double*)r, out);
+    else
+        k_scatter_scalar_by_id<float><<<nblocks(n), BLOCK, 0, st>>>(n, id, (const float*)r, out);
+}
+
+void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const uint8_t* type,
+                               int32_t* out)
+{
+    if (n <= 0) return;
+    k_scatter_type_by_id<<<nblocks(n), BLOCK, 0, st>>>(n, id, type, out);
+}
+
+}  // namespace mdpd

@@ -1,0 +1,118 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mdpd.h"
+
+namespace mdpd {
+
+// Device status bits, OR-ed by kernels into one word and mapped to MDPD_ERR_*.
+enum : uint32_t {
+    ST_NONFINITE = 1u,
+    ST_OUT_OF_BOX = 2u,
+    ST_OVERFLOW = 4u,
+    ST_TIMEOUT = 8u,
+};
+
+// Cell lattice and box (edge h >= r_c on every axis; x fastest).
+struct Geo {
+    int nc[3];
+    int periodic[3];
+    double lo[3], L[3], hi[3], h[3], inv_h[3];
+    int64_t ncell;
+};
+
+// Physical constants of Sec. 2.1 / Eq. 1, tables flattened [ti * 8 + tj].
+struct Phys {
+    double rc, rd, dt, hdt, kT;
+    double g[3];
+    uint32_t frozen;
+    int ntypes;
+    int xi_dist;
+    int rho_self;
+    uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
+    double A[64], B[64], gamma[64], sigma[64];
+};
+
+// Solid-voxel reflection mask (1 bit per voxel, x fastest); bits == nullptr
+// means no mask.
+struct MaskDev {
+    const uint32_t* bits;
+    int dim[3];
+    double voxel;
+    double origin[3];
+};
+
+// Master particle state, component-major: x[k * cap + i].
+struct Master {
+    double* x;
+    double* v;
+    double* a;
+    uint32_t* id;
+    uint8_t* type;
+};
+
+// Force-pass modes.
+enum ForceMode : int {
+    FM_EVAL = 0,    // write sum_j F_ij + g to `out`; no integration
+    FM_LAST = 1,    // second half-kick: v(t+dt) = v + dt/2 a; store a
+    FM_FUSED = 2,   // second half-kick, then the next step's half-kick,
+                    // drift and reflection
+};
+
+constexpr int OBS_PARTIALS = 16;   // doubles per block in the reduction
+
+// ---- launchers (binning / scan) -------------------------------------------
+void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, const Geo& geo,
+                      uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status);
+int scan_num_blocks(int64_t n);
+// Exclusive scan of in[0..n) into out[0..n]; tmp holds scan_num_blocks(n) + 1 words.
+void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint32_t* out,
+                           uint32_t* tmp);
+void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
+                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src);
+void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
+                      uint32_t* src);
+void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
+                   const uint32_t* cellof, const Master& in, const Master& out, bool gather_a,
+                   const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s);
+
+// ---- launchers (pair passes) -----------------------------------------------
+void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const Phys& ph,
+                    const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho);
+void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
+                  const Geo& geo, const Phys& ph, const MaskDev& mk, const void* pos4,
+                  const void* vel4, const void* rho, const uint32_t* cell_s,
+                  const uint32_t* start, const uint64_t* step_ptr, int step_offset,
+                  const Master& m, double* out, double* partials, uint32_t* status);
+int force_num_blocks(int n);
+void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
+                       const MaskDev& mk, const Master& m, uint32_t* status);
+void launch_reduce_obs(cudaStream_t st, const double* partials, int nblocks, double* obs,
+                       double* obs_sum, double* obs_count, uint64_t* step_ptr, int advance,
+                       double kT_dof_n);
+
+// ---- launchers (walls) -----------------------------------------------------
+void launch_mask_pack(cudaStream_t st, const uint8_t* mask, int64_t nvox, uint32_t* bits);
+void launch_wall_count(cudaStream_t st, const uint8_t* mask, const int dim[3], const int per[3],
+                       int R, int64_t R2, double lam, uint32_t key0, uint32_t key1,
+                       uint32_t* count);
+void launch_wall_emit(cudaStream_t st, const uint8_t* mask, const int dim[3],
+                      const uint32_t* count, const uint32_t* offset, double voxel,
+                      const double origin[3], uint32_t key0, uint32_t key1, int64_t base,
+                      int64_t cap, const Master& m, uint8_t wall_type);
+
+// ---- misc --------------------------------------------------------------------
+void launch_scatter_by_id(cudaStream_t st, int n, int64_t cap, const uint32_t* id,
+                          const double* vec3, double* out3);
+void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const uint32_t* id,
+                                 const void* rho_sorted, double* out);
+void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const uint8_t* type,
+                               int32_t* out);
+void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
+                       const double* vel3, const Geo& geo, const Master& m,
+                       const uint8_t* type_by_id, uint32_t* status);
+
+}  // namespace mdpd

@@ -1,0 +1,239 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances (per particle, ||f_gpu - f_ora|| / max(||f_ora||, rms f)):
+FP64 pair arithmetic 1e-12, FP32 pair arithmetic 1e-5.  Integer and index
+results (wall placement counts, ids, types) are compared exactly.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1903_10134_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-12, 1: 1e-5}
+RHO_TOL = {0: 1e-13, 1: 2e-6}
+
+
+@pytest.fixture(scope="module")
+def M():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10134_gb300 import mdpd
+    mdpd.lib()
+    return mdpd
+
+
+def rel_force_err(f, ref):
+    nrm = np.linalg.norm(ref, axis=1)
+    rms = math.sqrt(np.mean(nrm ** 2)) if len(nrm) else 1.0
+    den = np.maximum(nrm, rms)
+    return (np.linalg.norm(f - ref, axis=1) / den).max() if len(f) else 0.0
+
+
+def make(M, w, precision):
+    p = w.params.copy(precision=precision)
+    return M.System(p, w.pos, w.vel, w.type, w.seed), p
+
+
+CASES = [
+    # n, box, periodic, ntypes, seed
+    (3001, (8.0, 8.0, 8.0), (1, 1, 1), 1, 1),          # several blocks + ragged tail
+    (1500, (3.0, 9.0, 7.3), (1, 1, 1), 3, 2),          # 3 cells on x: images
+    (2200, (6.5, 5.0, 9.0), (1, 0, 1), 2, 3),          # reflecting y faces
+    (700, (2.4, 4.0, 3.5), (0, 0, 0), 2, 4),           # no periodic axis, nc < 3
+]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("case", CASES)
+def test_forces_and_density_match_oracle(M, case, precision):
+    n, L, per, nt, seed = case
+    w = I.tiny(n, L, seed, periodic=per, ntypes=nt, g=(0.01, -0.02, 0.005),
+               frozen_types=(1,) if nt > 1 else ())
+    s, p = make(M, w, precision)
+    f, rho = s.forces()
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
+    assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * max(1.0, o.rho.max())
+    assert rel_force_err(f, o.a) <= TOL[precision]
+    _, _, typ, rho2 = s.state()
+    assert np.array_equal(typ, w.type)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_gaussian_xi_and_rho_self(M, precision):
+    w = I.tiny(1200, (6.0, 6.0, 6.0), 8, ntypes=2, xi_dist=1, rho_self=1)
+    s, p = make(M, w, precision)
+    f, rho = s.forces()
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
+    assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * o.rho.max()
+    # Box-Muller goes through log/cos: allow the library functions' rounding
+    assert rel_force_err(f, o.a) <= (1e-11 if precision == 0 else 2e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_short_trajectory_matches_oracle(M, precision):
+    w = I.tiny(2500, (7.0, 7.0, 7.0), 5, ntypes=2, g=(0.05, 0.0, 0.0))
+    s, p = make(M, w, precision)
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
+    for _ in range(3):
+        s.step(4)
+        o.run(4)
+        x, v, _, rho = s.state()
+        L = np.array(p.box)
+        dx = (x - o.x + L / 2) % L - L / 2
+        # FP32 forces agree to ~1e-5 of rms f; over a few steps that moves v by
+        # ~dt * 1e-5 * |f| per half-kick and x by dt times that
+        tol_x = 1e-12 if precision == 0 else 2e-5
+        tol_v = 1e-10 if precision == 0 else 5e-4
+        assert np.abs(dx).max() < tol_x
+        assert np.abs(v - o.v).max() < tol_v * max(1.0, np.abs(o.v).max())
+    obs = s.observables()
+    ref = o.observables()
+    np.testing.assert_allclose(obs[:3], ref[:3], atol=1e-9 if precision == 0 else 2e-2)
+    np.testing.assert_allclose(obs[3:5], ref[3:5], rtol=1e-10 if precision == 0 else 1e-4)
+    np.testing.assert_allclose(obs[5:11], ref[5:11], rtol=1e-9 if precision == 0 else 1e-4,
+                               atol=1e-6 if precision == 0 else 1e-2)
+    assert obs[14] == ref[14] and obs[15] == ref[15] == 12
+    s.close()
+
+
+def test_walls_placement_and_reflection_match_oracle(M):
+    rng = np.random.default_rng(3)
+    nvox = (20, 16, 24)              # [z, y, x]
+    voxel = 0.5
+    f = I.gaussian_random_field(nvox, 2.5, rng)
+    mask = (f > np.quantile(f, 0.45)).astype(np.uint8)
+    L = (nvox[2] * voxel, nvox[1] * voxel, nvox[0] * voxel)
+    p = I.MDPDParams(box=L, periodic=(1, 1, 1), ntypes=2, frozen_types=(1,), g=(0.1, 0, 0),
+                     precision=0)
+    p.set_pair(0, 1, A=-30.0)
+    pore = np.flatnonzero(mask.reshape(-1) == 0)
+    npart = 800
+    pick = pore[rng.integers(0, pore.size, npart)]
+    idx = np.stack([pick % nvox[2], (pick // nvox[2]) % nvox[1], pick // (nvox[2] * nvox[1])], 1)
+    pos = (idx + rng.random((npart, 3))) * voxel
+    vel = I.maxwell_velocities(npart, 1.0, rng)
+    typ = np.zeros(npart, np.int32)
+    s = M.System(p, pos, vel, typ, 9)
+    s.set_walls(mask, voxel, (0.0, 0.0, 0.0), 6.0, 1.0, 1, 77)
+    wpos, _ = O.place_walls(mask, (1, 1, 1), voxel, (0.0, 0.0, 0.0), 6.0, 1.0, 77)
+    x, v, t, rho = s.state()
+    assert x.shape[0] == npart + wpos.shape[0]
+    assert np.array_equal(x[npart:], wpos)            # same FP64 operations: bit-exact
+    assert np.all(t[npart:] == 1) and np.all(v[npart:] == 0)
+    allpos = np.concatenate([pos, wpos])
+    alltyp = np.concatenate([typ, np.ones(len(wpos), np.int32)])
+    allvel = np.concatenate([vel, np.zeros_like(wpos)])
+    o = O.Oracle(p, allpos, allvel, alltyp, 9, mask=mask, voxel=voxel)
+    f, _ = s.forces()
+    assert rel_force_err(f, o.a) <= 1e-12
+    s.step(10)
+    o.run(10)
+    x, v, _, _ = s.state()
+    Lv = np.array(L)
+    dx = (x - o.x + Lv / 2) % Lv - Lv / 2
+    assert np.abs(dx).max() < 1e-11
+    assert np.abs(v - o.v).max() < 1e-9
+    # nothing entered a solid voxel
+    q = np.floor(x[:npart] / voxel).astype(int)
+    assert np.all(mask[q[:, 2], q[:, 1], q[:, 0]] == 0)
+    s.close()
+
+
+def test_graph_and_direct_launch_agree_bitwise(M):
+    w = I.tiny(4000, (9.0, 9.0, 9.0), 6)
+    a = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 3)
+    b = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 3)
+    b.set_option(M.OPT_GRAPH, 0)
+    a.step(7)
+    b.step(7)
+    xa, va, _, ra = a.state()
+    xb, vb, _, rb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+    a.step(5)
+    a2 = a.state()
+    # rerun from scratch: deterministic
+    c = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 3)
+    c.step(12)
+    assert np.array_equal(c.state()[0], a2[0])
+    for s in (a, b, c):
+        s.close()
+
+
+def test_set_state_roundtrip_and_resume(M):
+    w = I.tiny(1800, (6.0, 6.0, 6.0), 7)
+    p = w.params.copy(precision=0)
+    a = M.System(p, w.pos, w.vel, w.type, 5)
+    a.step(6)
+    x, v, _, _ = a.state()
+    b = M.System(p, w.pos, w.vel, w.type, 5)
+    b.set_state(x, v)
+    fa, ra = a.forces()
+    fb, rb = b.forces()
+    # b's step index is 0, a's is 6: densities agree, forces differ only by the draw
+    assert np.abs(ra - rb).max() < 1e-13
+    a.close()
+    b.close()
+
+
+def test_degenerate_inputs(M):
+    p = I.MDPDParams(box=(4.0, 4.0, 4.0), precision=0)
+    # empty system
+    s = M.System(p, np.zeros((0, 3)), np.zeros((0, 3)), np.zeros(0, np.int32), 1)
+    s.step(3)
+    assert s.state()[0].shape == (0, 3)
+    s.close()
+    # one particle: no neighbours, free flight
+    s = M.System(p, [[1.0, 1.0, 1.0]], [[0.5, 0.0, -0.25]], [0], 1)
+    f, rho = s.forces()
+    assert np.all(f == 0) and rho[0] == 0
+    s.step(10)
+    np.testing.assert_allclose(s.state()[0][0], [1.05, 1.0, 0.975], atol=1e-14)
+    s.close()
+    # coincident pair: density counts w_rho(0) each, the force skips r = 0
+    pos = np.array([[2.0, 2.0, 2.0], [2.0, 2.0, 2.0], [2.6, 2.0, 2.0]])
+    s = M.System(p, pos, np.zeros((3, 3)), np.zeros(3, np.int32), 1)
+    f, rho = s.forces()
+    o = O.Oracle(p, pos, np.zeros((3, 3)), np.zeros(3, np.int32), 1)
+    np.testing.assert_allclose(rho, o.rho, rtol=1e-14)
+    np.testing.assert_allclose(f, o.a, rtol=1e-12, atol=1e-12)
+    s.close()
+    # pair exactly at r_c: no interaction
+    pos = np.array([[1.0, 1.0, 1.0], [2.0, 1.0, 1.0]])
+    s = M.System(p, pos, np.zeros((2, 3)), np.zeros(2, np.int32), 1)
+    f, rho = s.forces()
+    assert np.all(f == 0)
+    s.close()
+
+
+def test_nonfinite_input_is_reported(M):
+    w = I.tiny(50, (4.0, 4.0, 4.0), 1)
+    pos = w.pos.copy()
+    pos[7, 1] = np.nan
+    with pytest.raises(M.MDPDError) as e:
+        M.System(w.params, pos, w.vel, w.type, 1)
+    assert e.value.name == "NONFINITE"
+
+
+@pytest.mark.parametrize("name", ["bulk", "slab"])
+def test_workload_sampled_parity(M, name):
+    """Full-size paper-shaped workloads, FP32 as benchmarked: forces of a
+    sample of particles against the oracle, densities of all particles."""
+    w = I.bulk() if name == "bulk" else I.slab()
+    s, p = make(M, w, 1)
+    f, rho = s.forces()
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed, use_cells=True)
+    assert np.abs(rho - o.rho).max() <= RHO_TOL[1] * o.rho.max()
+    idx = np.random.default_rng(0).choice(w.n, 400, replace=False)
+    ref = o.forces_subset(idx, rho=o.rho)
+    rms = math.sqrt(np.mean(np.sum(o.a ** 2, axis=1)))
+    err = np.linalg.norm(f[idx] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
+    assert err.max() <= TOL[1]
+    s.close()
