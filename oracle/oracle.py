@@ -243,6 +243,8 @@ class Oracle:
         if rc != 0:
             raise RuntimeError("oracle run failed")
         self.step = int(step.value)
+        if nsteps > 0:
+            self.virial = last[5:11].copy()
         return last, s / max(nsteps, 1)
 
     def observables(self) -> np.ndarray:

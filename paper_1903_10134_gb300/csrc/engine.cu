@@ -301,7 +301,8 @@ int sync_check(mdpd_handle* h)
 
 void record(mdpd_handle* h, cudaEvent_t* evs, int k)
 {
-    if (evs) cudaEventRecord(evs[k], h->stream);
+    // external record: inside a stream capture this becomes an event-record node
+    if (evs) cudaEventRecordWithFlags(evs[k], h->stream, cudaEventRecordExternal);
 }
 
 // Bin: count, scan, scatter, per-cell sort, gather into the other buffer.

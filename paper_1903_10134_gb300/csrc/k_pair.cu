@@ -241,7 +241,7 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
                                 f[1] += fp * dy;
                                 f[2] += fp * dz;
                                 ++npair;
-                                const T fv = T(0.5) * fc * rinv * rinv;
+                                const T fv = T(0.5) * fc * rinv;          // 0.5 d_a F^C e_b = 0.5 fc d_a d_b / r
                                 W[0] += fv * dx * dx;
                                 W[1] += fv * dy * dy;
                                 W[2] += fv * dz * dz;

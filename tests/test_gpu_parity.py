@@ -60,6 +60,11 @@ def test_forces_and_density_match_oracle(M, case, precision):
     o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
     assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * max(1.0, o.rho.max())
     assert rel_force_err(f, o.a) <= TOL[precision]
+    obs = s.observables()
+    ref = o.observables()
+    scale = np.abs(ref[5:8]).max()
+    assert np.abs(obs[5:11] - ref[5:11]).max() <= (1e-11 if precision == 0 else 1e-5) * scale
+    assert obs[14] == ref[14]
     _, _, typ, rho2 = s.state()
     assert np.array_equal(typ, w.type)
     s.close()
