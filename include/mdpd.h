@@ -191,6 +191,28 @@ int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps,
  * issues. */
 int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_step);
 
+/* Local densities rho_i for callers that cannot allocate device memory.
+ * There is no counterpart in the paper; this is a service of the library.
+ * Some callers may not let a library allocate: a plugin inside a host
+ * application that owns the whole device-memory budget and passes in only
+ * its buffers, or code on a latency-critical path where cudaMalloc/cudaFree
+ * (which can synchronise the device) are not allowed.  This entry point runs
+ * the binning and density kernels with all temporaries in one fixed
+ * __device__ array of the library (about 4.3 MB, held by every GPU that
+ * loads the library until the process exits); it calls no allocator.
+ * params: box, periodic, rc, rd, precision and rho_self are used.
+ * pos: device array of 3n doubles (interleaved xyz, inside the box on
+ * non-periodic axes); rho: device array of n doubles, written in input order.
+ * Limits: n <= 65536 and at most 32768 cells of edge >= rc; larger inputs
+ * fail with MDPD_ERR_INVALID_ARG (message from mdpd_last_error(NULL)).
+ * Asynchronous on cuda_stream (NULL = legacy default stream).  The first call
+ * on each device looks up the array's device address; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and give wrong
+ * results. */
+int mdpd_density_noalloc(const mdpd_params* params, int64_t n, const double* pos,
+                         double* rho, void* cuda_stream);
+
 void mdpd_destroy(mdpd_handle* h);
 
 /* Message of the last error on h (or of the last failed mdpd_create when h is

@@ -564,6 +564,11 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
 
 }  // namespace
 
+namespace mdpd {
+// Error text for entry points that have no handle (read by mdpd_last_error(NULL)).
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace mdpd
+
 extern "C" {
 
 int mdpd_create(const mdpd_params* params, int64_t n, const double* pos, const double* vel,

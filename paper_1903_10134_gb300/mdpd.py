@@ -87,7 +87,7 @@ SYMBOLS = (
     "mdpd_set_state", "mdpd_set_state_dev", "mdpd_forces", "mdpd_forces_dev",
     "mdpd_observables", "mdpd_observables_mean", "mdpd_pair_count", "mdpd_set_option",
     "mdpd_profile",
-    "mdpd_describe", "mdpd_destroy", "mdpd_last_error",
+    "mdpd_describe", "mdpd_density_noalloc", "mdpd_destroy", "mdpd_last_error",
 )
 
 
@@ -124,6 +124,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_set_option.argtypes = [P, i32, i64]
     L.mdpd_profile.argtypes = [P, P, C.POINTER(i64), C.POINTER(i64)]
     L.mdpd_describe.argtypes = [P, P, C.POINTER(i32)]
+    L.mdpd_density_noalloc.argtypes = [P, i64, P, P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -300,6 +301,16 @@ def mdpd_describe(h):
     lps = C.c_int32()
     _check(lib().mdpd_describe(h, _p(nc), C.byref(lps)), h)
     return nc.tolist(), int(lps.value)
+
+
+def mdpd_density_noalloc(params, pos_t, rho_t, stream=None):
+    """Densities of the particles at device positions pos_t ((n, 3) float64) into
+    rho_t ((n,) float64) without any device allocation by the library (fixed
+    internal scratch; n <= 65536, <= 32768 cells).  Asynchronous on `stream`."""
+    cp = to_c_params(params)
+    n = int(pos_t.shape[0])
+    _check(lib().mdpd_density_noalloc(C.byref(cp), n, _tptr(pos_t), _tptr(rho_t),
+                                      _stream_ptr(stream)))
 
 
 def mdpd_destroy(h):
