@@ -82,6 +82,7 @@ typedef struct mdpd_handle mdpd_handle;
  * so that xi_ij = xi_ji (Sec. 2.1).  cuda_stream: a cudaStream_t to run on,
  * or NULL for a stream the handle creates and owns.
  * The density and forces of the initial state are evaluated (step index 0).
+ * At most 2^27 particles (including wall particles).
  * Errors: INVALID_ARG (n < 0, ntypes out of range, r_d > r_c, non-positive
  * dt/r_c/box, a periodic axis shorter than 3 r_c, a type out of range),
  * OOM, CUDA. */
@@ -174,8 +175,14 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *                      0: launch kernels one by one.
  *   MDPD_OPT_PROFILE   k > 0: record CUDA events around every kernel class of
  *                      the next steps (up to k steps); 0: off.
+ *   MDPD_OPT_KERNELS   MDPD_KERNELS_NLIST (default): the density pass records
+ *                      each mobile particle's partners within r_c and the
+ *                      force pass walks that list; MDPD_KERNELS_SCAN: both
+ *                      passes scan the 27 neighbour cells directly.  Same
+ *                      results up to FP summation order.
  */
-enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2 };
+enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3 };
+enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
 /* Kernel classes reported by mdpd_profile(). */

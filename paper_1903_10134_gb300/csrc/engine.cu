@@ -15,7 +15,7 @@ using namespace mdpd;
 
 namespace {
 
-constexpr int64_t MAX_PARTICLES = int64_t(1) << 30;
+constexpr int64_t MAX_PARTICLES = int64_t(1) << 27;   // neighbour-list entries hold j << 5
 constexpr int64_t MAX_SCAN = int64_t(4096) * 4096;   // limit of the two-level scan
 constexpr int EV_PER_STEP = 5;                        // profile events per step
 
@@ -64,6 +64,9 @@ struct mdpd_handle {
     double* fout = nullptr;      // 3 * cap staging / force output
     uint8_t* type_by_id = nullptr;
     uint32_t* mask_bits = nullptr;
+    uint32_t* nl = nullptr;          // NL_SLOTS * cap neighbour-list entries
+    uint32_t* nl_count = nullptr;    // cap
+    int kernels = MDPD_KERNELS_NLIST;
     bool walls_set = false;
     std::vector<int32_t> h_type;
     int64_t steps_host = 0;
@@ -149,6 +152,8 @@ void free_particles(mdpd_handle* h)
     dfree(h->partials);
     dfree(h->fout);
     dfree(h->type_by_id);
+    dfree(h->nl);
+    dfree(h->nl_count);
 }
 
 int alloc_particles(mdpd_handle* h, int64_t cap)
@@ -175,6 +180,8 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->partials, (size_t)force_num_blocks((int)c) * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
+    if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->nl_count, c * sizeof(uint32_t));
     if (!rc) h->cap = (int64_t)c;
     return rc;
 }
@@ -322,15 +329,24 @@ void enqueue_bin(mdpd_handle* h, bool gather_a)
 
 void enqueue_density(mdpd_handle* h)
 {
-    launch_density(h->stream, h->precision, (int)h->n, h->geo, h->ph, h->pos4, h->cell_s,
-                   h->start, h->rho);
+    if (h->kernels == MDPD_KERNELS_NLIST)
+        launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
+                          h->cell_s, h->start, h->rho, h->nl, h->nl_count);
+    else
+        launch_density(h->stream, h->precision, (int)h->n, h->geo, h->ph, h->pos4, h->cell_s,
+                       h->start, h->rho);
 }
 
 void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 {
-    launch_force(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk, h->pos4,
-                 h->vel4, h->rho, h->cell_s, h->start, h->step, step_offset, master(h, h->cur),
-                 out, h->partials, h->status);
+    if (h->kernels == MDPD_KERNELS_NLIST)
+        launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
+                        h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->nl, h->nl_count,
+                        h->step, step_offset, master(h, h->cur), out, h->partials, h->status);
+    else
+        launch_force(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
+                     h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->step, step_offset,
+                     master(h, h->cur), out, h->partials, h->status);
 }
 
 void enqueue_reduce(mdpd_handle* h, int advance)
@@ -913,6 +929,13 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
     switch (option) {
     case MDPD_OPT_GRAPH:
         h->use_graph = value != 0;
+        return MDPD_OK;
+    case MDPD_OPT_KERNELS:
+        if (value != MDPD_KERNELS_NLIST && value != MDPD_KERNELS_SCAN)
+            return h->fail(MDPD_ERR_INVALID_ARG, "unknown kernel variant");
+        CK(cudaStreamSynchronize(h->stream));
+        h->kernels = (int)value;
+        destroy_graphs(h);
         return MDPD_OK;
     case MDPD_OPT_PROFILE: {
         if (value < 0 || value > (int64_t(1) << 20)) return h->fail(MDPD_ERR_INVALID_ARG, "profile steps out of range");

@@ -6,69 +6,11 @@
 // (Algorithm 1), plus per-block FP64 partial sums of the observables.
 // One thread per particle in cell order; neighbours are the particles of the
 // 27 surrounding cells (edge >= r_c), read through the read-only data cache.
-#include "mdpd_internal.cuh"
-#include "philox.cuh"
-#include "vec.cuh"
+#include "pair.cuh"
 
 namespace mdpd {
 
 namespace {
-
-constexpr int PAIR_BLOCK = 128;
-constexpr int NOBS = 14;   // momentum 3, sum v^2 3, virial 6, mobile count 1, pairs 1
-
-__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
-
-template <typename T>
-__device__ __forceinline__ T xi_of(U4 w, int dist)
-{
-    if (dist == 0) return xi_uniform<T>(w.x);
-    if constexpr (sizeof(T) == 4) return xi_gauss_f(w.x, w.y);
-    else return xi_gauss_d(w.x, w.y);
-}
-
-// Drift by dt with velocity v, wrap periodic axes, and undo the drift with a
-// negated velocity if the new position is beyond a non-periodic face or in a
-// solid voxel.  Explicit round-to-nearest operations keep each product and
-// sum separately rounded.
-__device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], const Geo& geo,
-                                              const MaskDev& mk, double dt)
-{
-    double xn[3];
-    bool blocked = false;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        xn[k] = __dadd_rn(x[k], __dmul_rn(dt, v[k]));
-        if (geo.periodic[k]) {
-            if (xn[k] >= geo.hi[k]) xn[k] = __dsub_rn(xn[k], geo.L[k]);
-            else if (xn[k] < geo.lo[k]) xn[k] = __dadd_rn(xn[k], geo.L[k]);
-        } else if (xn[k] < geo.lo[k] || xn[k] >= geo.hi[k]) {
-            blocked = true;
-        }
-    }
-    if (!blocked && mk.bits != nullptr) {
-        bool inside = true;
-        int64_t q[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const double f = floor(__ddiv_rn(__dsub_rn(xn[k], mk.origin[k]), mk.voxel));
-            if (!(f >= 0.0) || f >= (double)mk.dim[k]) inside = false;
-            q[k] = inside ? (int64_t)f : 0;
-        }
-        if (inside) {
-            const int64_t idx = q[0] + (int64_t)mk.dim[0] * (q[1] + (int64_t)mk.dim[1] * q[2]);
-            blocked = (mk.bits[idx >> 5] >> (idx & 31)) & 1u;
-        }
-    }
-    if (blocked) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v[k] = -v[k];
-    } else {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) x[k] = xn[k];
-    }
-}
 
 template <typename T>
 __global__ void __launch_bounds__(PAIR_BLOCK)
@@ -127,27 +69,9 @@ k_density(int n, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ po
     rho_out[s] = acc;
 }
 
-// Deterministic block sum of NOBS doubles into partials[blockIdx.x * OBS_PARTIALS + k].
-__device__ __forceinline__ void block_obs_store(double (&o)[NOBS], double* __restrict__ partials)
-{
-    __shared__ double sh[PAIR_BLOCK / 32][NOBS];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) {
-        double v = o[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[warp][k] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NOBS) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < PAIR_BLOCK / 32; ++w) v += sh[w][threadIdx.x];
-        partials[(int64_t)blockIdx.x * OBS_PARTIALS + threadIdx.x] = v;
-    }
-}
-
+// Direct-scan force pass: each thread tests the particles of its 27 neighbour
+// cells itself.  Kept as the baseline variant and for rows of cells too dense
+// for a neighbour list.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(PAIR_BLOCK)
 k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
@@ -157,25 +81,16 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         const uint64_t* __restrict__ step_ptr, int step_offset, Master m,
         double* __restrict__ out, double* __restrict__ partials, uint32_t* __restrict__ status)
 {
-    __shared__ T sA[64], sB[64], sG[64], sS[64];
-    for (int t = threadIdx.x; t < 64; t += blockDim.x) {
-        sA[t] = (T)ph.A[t];
-        sB[t] = (T)ph.B[t];
-        sG[t] = (T)ph.gamma[t];
-        sS[t] = (T)ph.sigma[t];
-    }
+    __shared__ PairTables<T> tab;
+    load_tables(tab, ph);
     __syncthreads();
-
     const uint64_t step = *step_ptr + (uint64_t)step_offset;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double obs[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) obs[k] = 0.0;
-
     if (s < n) {
-        const T rc2 = (T)(ph.rc * ph.rc), rd2 = (T)(ph.rd * ph.rd);
-        const T inv_rc = (T)(1.0 / ph.rc), inv_rd = (T)(1.0 / ph.rd);
-        const T inv_sqrt_dt = (T)(1.0 / sqrt(ph.dt));
+        const PairConst<T> c(ph);
         const auto pi = pos4[s];
         const auto vi = vel4[s];
         const T rho_i = rho[s];
@@ -186,34 +101,23 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         T W[6] = { T(0), T(0), T(0), T(0), T(0), T(0) };
         int npair = 0;
         if (mobile) {
-            const uint32_t c = cell_s[s];
-            const int q0 = (int)(c % (uint32_t)geo.nc[0]);
-            const int q1 = (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]);
-            const int q2 = (int)(c / ((uint32_t)geo.nc[0] * (uint32_t)geo.nc[1]));
-            const T* tA = sA + ti * 8;
-            const T* tB = sB + ti * 8;
-            const T* tG = sG + ti * 8;
-            const T* tS = sS + ti * 8;
+            int q0, q1, q2;
+            cell_coords(cell_s[s], geo, q0, q1, q2);
+            const T* tA = tab.A + ti * 8;
+            const T* tB = tab.B + ti * 8;
+            const T* tG = tab.G + ti * 8;
+            const T* tS = tab.S + ti * 8;
             for (int oz = -1; oz <= 1; ++oz) {
-                int z = q2 + oz;
-                if (z < 0 || z >= geo.nc[2]) {
-                    if (!geo.periodic[2]) continue;
-                    z = z < 0 ? z + geo.nc[2] : z - geo.nc[2];
-                }
+                const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
+                if (z < 0) continue;
                 const T sz = pi.z - (T)oz * (T)geo.h[2];
                 for (int oy = -1; oy <= 1; ++oy) {
-                    int y = q1 + oy;
-                    if (y < 0 || y >= geo.nc[1]) {
-                        if (!geo.periodic[1]) continue;
-                        y = y < 0 ? y + geo.nc[1] : y - geo.nc[1];
-                    }
+                    const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
+                    if (y < 0) continue;
                     const T sy = pi.y - (T)oy * (T)geo.h[1];
                     for (int ox = -1; ox <= 1; ++ox) {
-                        int x = q0 + ox;
-                        if (x < 0 || x >= geo.nc[0]) {
-                            if (!geo.periodic[0]) continue;
-                            x = x < 0 ? x + geo.nc[0] : x - geo.nc[0];
-                        }
+                        const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
+                        if (x < 0) continue;
                         const T sx = pi.x - (T)ox * (T)geo.h[0];
                         const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
                         const uint32_t b = start[nc], e = start[nc + 1];
@@ -221,89 +125,18 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
                             const auto pj = pos4[j];
                             const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
                             const T r2 = dx * dx + dy * dy + dz * dz;
-                            if (r2 < rc2 && r2 > T(0)) {
+                            if (r2 < c.rc2 && r2 > T(0)) {
                                 const auto vj = vel4[j];
-                                const T rho_j = rho[j];
-                                const uint32_t tj = unpack_u32(pj.w);
-                                const uint32_t id_j = unpack_u32(vj.w);
-                                const T rinv = rsqrt_t(r2);
-                                const T r = r2 * rinv;
-                                const T wc = T(1) - r * inv_rc;
-                                T fc = tA[tj] * wc;
-                                if (r2 < rd2) fc += tB[tj] * (rho_i + rho_j) * (T(1) - r * inv_rd);
-                                const T ev = (dx * (vi.x - vj.x) + dy * (vi.y - vj.y) +
-                                              dz * (vi.z - vj.z)) * rinv;
-                                const T fd = -tG[tj] * wc * wc * ev;
-                                const U4 w = pair_draw(id_i, id_j, step, ph.key0, ph.key1);
-                                const T fr = tS[tj] * wc * xi_of<T>(w, ph.xi_dist) * inv_sqrt_dt;
-                                const T fp = (fc + fd + fr) * rinv;
-                                f[0] += fp * dx;
-                                f[1] += fp * dy;
-                                f[2] += fp * dz;
+                                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i, rho[j],
+                                          unpack_u32(pj.w), id_i, unpack_u32(vj.w), step, ph, f, W);
                                 ++npair;
-                                const T fv = T(0.5) * fc * rinv;          // 0.5 d_a F^C e_b = 0.5 fc d_a d_b / r
-                                W[0] += fv * dx * dx;
-                                W[1] += fv * dy * dy;
-                                W[2] += fv * dz * dz;
-                                W[3] += fv * dx * dy;
-                                W[4] += fv * dx * dz;
-                                W[5] += fv * dy * dz;
                             }
                         }
                     }
                 }
             }
         }
-        double a[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) a[k] = mobile ? (double)f[k] + ph.g[k] : 0.0;
-        uint32_t st = 0;
-        if (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[2])) st |= ST_NONFINITE;
-        double v[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
-        if (MODE == FM_EVAL) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) out[k * cap + s] = a[k];
-        } else if (mobile) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
-        }
-        if (mobile) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                obs[k] = v[k];
-                obs[3 + k] = v[k] * v[k];
-            }
-#pragma unroll
-            for (int k = 0; k < 6; ++k) obs[6 + k] = (double)W[k];
-            obs[12] = 1.0;
-            obs[13] = (double)npair;
-        }
-        if (MODE == FM_LAST && mobile) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                m.v[k * cap + s] = v[k];
-                m.a[k * cap + s] = a[k];
-            }
-        }
-        if (MODE == FM_FUSED && mobile) {
-            double x[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                x[k] = m.x[k * cap + s];
-                v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
-            }
-            drift_reflect(x, v, geo, mk, ph.dt);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                m.x[k * cap + s] = x[k];
-                m.v[k * cap + s] = v[k];
-            }
-        }
-        if (MODE != FM_EVAL && (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])))
-            st |= ST_NONFINITE;
-        if (st) atomicOr(status, st);
+        force_finish<T, MODE>(s, mobile, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     }
     block_obs_store(obs, partials);
 }
@@ -329,43 +162,50 @@ __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, M
     if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) atomicOr(status, ST_NONFINITE);
 }
 
-// One block: fixed-order sum of the per-block partials, then the derived
-// observables; with `advance` the step counter moves on and the running sums
-// accumulate.
-__global__ void __launch_bounds__(256)
+// One block: fixed-order sum of the per-block partials (laid out [k][block]),
+// then the derived observables; with `advance` the step counter moves on and
+// the running sums accumulate.
+constexpr int RED_THREADS = 512;
+
+__global__ void __launch_bounds__(RED_THREADS)
 k_reduce_obs(const double* __restrict__ partials, int nblocks, double* __restrict__ obs,
              double* __restrict__ obs_sum, double* __restrict__ obs_count,
              uint64_t* __restrict__ step_ptr, int advance)
 {
-    __shared__ double sh[256][NOBS];
+    __shared__ double sh[RED_THREADS / 32][NOBS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double acc[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += 256)
+    for (int b = threadIdx.x; b < nblocks; b += RED_THREADS)
 #pragma unroll
-        for (int k = 0; k < NOBS; ++k) acc[k] += partials[(int64_t)b * OBS_PARTIALS + k];
+        for (int k = 0; k < NOBS; ++k) acc[k] += partials[(int64_t)k * nblocks + b];
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) sh[threadIdx.x][k] = acc[k];
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
+    for (int k = 0; k < NOBS; ++k) {
+        double v = acc[k];
 #pragma unroll
-            for (int k = 0; k < NOBS; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + w][k];
-        __syncthreads();
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[warp][k] = v;
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
+        double t[NOBS];
+        for (int k = 0; k < NOBS; ++k) {
+            t[k] = 0.0;
+            for (int w = 0; w < RED_THREADS / 32; ++w) t[k] += sh[w][k];
+        }
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
         double o[MDPD_NUM_OBS];
-        for (int k = 0; k < 3; ++k) o[k] = sh[0][k];
-        o[3] = 0.5 * (sh[0][3] + sh[0][4] + sh[0][5]);
-        const double nm = sh[0][12];
+        for (int k = 0; k < 3; ++k) o[k] = t[k];
+        o[3] = 0.5 * (t[3] + t[4] + t[5]);
+        const double nm = t[12];
         o[4] = nm > 1.0 ? 2.0 * o[3] / (3.0 * (nm - 1.0)) : 0.0;
-        for (int k = 0; k < 6; ++k) o[5 + k] = sh[0][6 + k];
-        for (int k = 0; k < 3; ++k) o[11 + k] = sh[0][3 + k];
+        for (int k = 0; k < 6; ++k) o[5 + k] = t[6 + k];
+        for (int k = 0; k < 3; ++k) o[11 + k] = t[3 + k];
         o[14] = nm;
         o[15] = (double)step;
         for (int k = 0; k < MDPD_NUM_OBS; ++k) obs[k] = o[k];
-        obs[2 * MDPD_NUM_OBS + 1] = sh[0][13];     // directed pairs with r < r_c
+        obs[2 * MDPD_NUM_OBS + 1] = t[13];     // directed pairs with r < r_c
         if (advance) {
             for (int k = 0; k < MDPD_NUM_OBS; ++k) obs_sum[k] += o[k];
             *obs_count += 1.0;
@@ -447,7 +287,7 @@ void launch_reduce_obs(cudaStream_t st, const double* partials, int nblocks, dou
                        double* obs_sum, double* obs_count, uint64_t* step_ptr, int advance,
                        double)
 {
-    k_reduce_obs<<<1, 256, 0, st>>>(partials, nblocks, obs, obs_sum, obs_count, step_ptr,
+    k_reduce_obs<<<1, RED_THREADS, 0, st>>>(partials, nblocks, obs, obs_sum, obs_count, step_ptr,
                                     advance);
 }
 

@@ -88,6 +88,18 @@ void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t
                   const uint32_t* start, const uint64_t* step_ptr, int step_offset,
                   const Master& m, double* out, double* partials, uint32_t* status);
 int force_num_blocks(int n);
+// Density pass that also writes the force partners of mobile particles
+// (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
+void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                       const Phys& ph, const void* pos4, const uint32_t* cell_s,
+                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count);
+void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
+                     const Geo& geo, const Phys& ph, const MaskDev& mk, const void* pos4,
+                     const void* vel4, const void* rho, const uint32_t* cell_s,
+                     const uint32_t* start, const uint32_t* nl, const uint32_t* nl_count,
+                     const uint64_t* step_ptr, int step_offset, const Master& m, double* out,
+                     double* partials, uint32_t* status);
+constexpr int NL_SLOTS = 64;      // must equal NL_MAX of the kernels
 void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                        const MaskDev& mk, const Master& m, uint32_t* status);
 void launch_reduce_obs(cudaStream_t st, const double* partials, int nblocks, double* obs,

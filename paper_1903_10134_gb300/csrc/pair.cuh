@@ -1,0 +1,232 @@
+// Device pieces shared by the density and force kernels: the pair force of
+// Sec. 2.1 / Eq. 1 (arXiv:1903.10134), the velocity-Verlet epilogue of
+// Algorithm 1 with the wall reflection, and the FP64 block reduction of the
+// observables.
+#pragma once
+
+#include "mdpd_internal.cuh"
+#include "philox.cuh"
+#include "vec.cuh"
+
+namespace mdpd {
+
+constexpr int PAIR_BLOCK = 128;
+constexpr int NOBS = 14;     // momentum 3, sum v^2 3, virial 6, mobile count 1, pairs 1
+constexpr int NL_MAX = NL_SLOTS;   // neighbour-list slots per particle (more: direct scan)
+
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T xi_of(U4 w, int dist)
+{
+    if (dist == 0) return xi_uniform<T>(w.x);
+    if constexpr (sizeof(T) == 4) return xi_gauss_f(w.x, w.y);
+    else return xi_gauss_d(w.x, w.y);
+}
+
+// Per-type-pair tables in shared memory, row ti: A, B, gamma, sigma.
+template <typename T>
+struct PairTables {
+    T A[64], B[64], G[64], S[64];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_tables(PairTables<T>& t, const Phys& ph)
+{
+    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+        t.A[k] = (T)ph.A[k];
+        t.B[k] = (T)ph.B[k];
+        t.G[k] = (T)ph.gamma[k];
+        t.S[k] = (T)ph.sigma[k];
+    }
+}
+
+template <typename T>
+struct PairConst {
+    T rc2, rd2, inv_rc, inv_rd, inv_sqrt_dt;
+    __device__ explicit PairConst(const Phys& ph)
+        : rc2((T)(ph.rc * ph.rc)), rd2((T)(ph.rd * ph.rd)), inv_rc((T)(1.0 / ph.rc)),
+          inv_rd((T)(1.0 / ph.rd)), inv_sqrt_dt((T)(1.0 / sqrt(ph.dt)))
+    {
+    }
+};
+
+// Add the force of j on i (separation d = r_i - r_j, 0 < r2 < r_c^2) to f and
+// the conservative virial 0.5 d_a F^C e_b to W:
+//   F = [A w_C + B (rho_i + rho_j) w_d [r < r_d] - gamma w_C^2 (e.v_ij)
+//        + sigma w_C xi_ij / sqrt(dt)] e,   w_C = 1 - r/r_c, w_d = 1 - r/r_d.
+template <typename T, typename V4>
+__device__ __forceinline__ void pair_term(const PairConst<T>& c, const T* tA, const T* tB,
+                                          const T* tG, const T* tS, T dx, T dy, T dz, T r2,
+                                          const V4& vi, const V4& vj, T rho_i, T rho_j,
+                                          uint32_t tj, uint32_t id_i, uint32_t id_j,
+                                          uint64_t step, const Phys& ph, T (&f)[3], T (&W)[6])
+{
+    const T rinv = rsqrt_t(r2);
+    const T r = r2 * rinv;
+    const T wc = T(1) - r * c.inv_rc;
+    T fc = tA[tj] * wc;
+    if (r2 < c.rd2) fc += tB[tj] * (rho_i + rho_j) * (T(1) - r * c.inv_rd);
+    const T ev = (dx * (vi.x - vj.x) + dy * (vi.y - vj.y) + dz * (vi.z - vj.z)) * rinv;
+    const T fd = -tG[tj] * wc * wc * ev;
+    const U4 w = pair_draw(id_i, id_j, step, ph.key0, ph.key1);
+    const T fr = tS[tj] * wc * xi_of<T>(w, ph.xi_dist) * c.inv_sqrt_dt;
+    const T fp = (fc + fd + fr) * rinv;
+    f[0] += fp * dx;
+    f[1] += fp * dy;
+    f[2] += fp * dz;
+    const T fv = T(0.5) * fc * rinv;      // 0.5 d_a F^C e_b = 0.5 fc d_a d_b / r
+    W[0] += fv * dx * dx;
+    W[1] += fv * dy * dy;
+    W[2] += fv * dz * dz;
+    W[3] += fv * dx * dy;
+    W[4] += fv * dx * dz;
+    W[5] += fv * dy * dz;
+}
+
+// Drift by dt with velocity v, wrap periodic axes, and undo the drift with a
+// negated velocity if the new position is beyond a non-periodic face or in a
+// solid voxel.  Explicit round-to-nearest operations keep each product and
+// sum separately rounded.
+__device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], const Geo& geo,
+                                              const MaskDev& mk, double dt)
+{
+    double xn[3];
+    bool blocked = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        xn[k] = __dadd_rn(x[k], __dmul_rn(dt, v[k]));
+        if (geo.periodic[k]) {
+            if (xn[k] >= geo.hi[k]) xn[k] = __dsub_rn(xn[k], geo.L[k]);
+            else if (xn[k] < geo.lo[k]) xn[k] = __dadd_rn(xn[k], geo.L[k]);
+        } else if (xn[k] < geo.lo[k] || xn[k] >= geo.hi[k]) {
+            blocked = true;
+        }
+    }
+    if (!blocked && mk.bits != nullptr) {
+        bool inside = true;
+        int64_t q[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const double f = floor(__ddiv_rn(__dsub_rn(xn[k], mk.origin[k]), mk.voxel));
+            if (!(f >= 0.0) || f >= (double)mk.dim[k]) inside = false;
+            q[k] = inside ? (int64_t)f : 0;
+        }
+        if (inside) {
+            const int64_t idx = q[0] + (int64_t)mk.dim[0] * (q[1] + (int64_t)mk.dim[1] * q[2]);
+            blocked = (mk.bits[idx >> 5] >> (idx & 31)) & 1u;
+        }
+    }
+    if (blocked) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = -v[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = xn[k];
+    }
+}
+
+// Everything after the pair sum of mobile-or-frozen particle s: acceleration,
+// the half-kick(s), drift and reflection by MODE, and the observables.
+template <typename T, int MODE>
+__device__ __forceinline__ void force_finish(int s, bool mobile, const T (&f)[3],
+                                             const T (&W)[6], int npair, int64_t cap,
+                                             const Geo& geo, const Phys& ph, const MaskDev& mk,
+                                             const Master& m, double* __restrict__ out,
+                                             double (&obs)[NOBS], uint32_t* status)
+{
+    double a[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a[k] = mobile ? (double)f[k] + ph.g[k] : 0.0;
+    uint32_t st = 0;
+    if (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[2])) st |= ST_NONFINITE;
+    double v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
+    if (MODE == FM_EVAL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[k * cap + s] = a[k];
+    } else if (mobile) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
+    }
+    if (mobile) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            obs[k] = v[k];
+            obs[3 + k] = v[k] * v[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) obs[6 + k] = (double)W[k];
+        obs[12] = 1.0;
+        obs[13] = (double)npair;
+    }
+    if (MODE == FM_LAST && mobile) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            m.v[k * cap + s] = v[k];
+            m.a[k * cap + s] = a[k];
+        }
+    }
+    if (MODE == FM_FUSED && mobile) {
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            x[k] = m.x[k * cap + s];
+            v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
+        }
+        drift_reflect(x, v, geo, mk, ph.dt);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            m.x[k * cap + s] = x[k];
+            m.v[k * cap + s] = v[k];
+        }
+    }
+    if (MODE != FM_EVAL && (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])))
+        st |= ST_NONFINITE;
+    if (st) atomicOr(status, st);
+}
+
+// Deterministic block sum of NOBS doubles into partials[k * gridDim.x + blockIdx.x]
+// (all threads of the block must call it).
+__device__ __forceinline__ void block_obs_store(double (&o)[NOBS], double* __restrict__ partials)
+{
+    __shared__ double sh[PAIR_BLOCK / 32][NOBS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) {
+        double v = o[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sh[warp][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NOBS) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < PAIR_BLOCK / 32; ++w) v += sh[w][threadIdx.x];
+        partials[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+// Decompose a cell id into lattice coordinates.
+__device__ __forceinline__ void cell_coords(uint32_t c, const Geo& geo, int& q0, int& q1, int& q2)
+{
+    q0 = (int)(c % (uint32_t)geo.nc[0]);
+    q1 = (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]);
+    q2 = (int)(c / ((uint32_t)geo.nc[0] * (uint32_t)geo.nc[1]));
+}
+
+// Neighbour cell along one axis: -1 if it falls off a non-periodic face.
+__device__ __forceinline__ int neighbour_index(int q, int o, int nc, int periodic)
+{
+    int z = q + o;
+    if (z < 0 || z >= nc) {
+        if (!periodic) return -1;
+        z = z < 0 ? z + nc : z - nc;
+    }
+    return z;
+}
+
+}  // namespace mdpd

@@ -22,6 +22,9 @@ MAX_TYPES = 8
 NUM_OBS = 16
 OPT_GRAPH = 1
 OPT_PROFILE = 2
+OPT_KERNELS = 3
+KERNELS_NLIST = 0
+KERNELS_SCAN = 1
 KCLASS = ("bin", "density", "force", "other")
 
 ERRORS = {

@@ -49,13 +49,15 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernels", [0, 1])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", CASES)
-def test_forces_and_density_match_oracle(M, case, precision):
+def test_forces_and_density_match_oracle(M, case, precision, kernels):
     n, L, per, nt, seed = case
     w = I.tiny(n, L, seed, periodic=per, ntypes=nt, g=(0.01, -0.02, 0.005),
                frozen_types=(1,) if nt > 1 else ())
     s, p = make(M, w, precision)
+    s.set_option(M.OPT_KERNELS, kernels)
     f, rho = s.forces()
     o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
     assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * max(1.0, o.rho.max())
@@ -242,3 +244,36 @@ def test_workload_sampled_parity(M, name):
     err = np.linalg.norm(f[idx] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
     assert err.max() <= TOL[1]
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_dense_particles_overflow_the_list(M, precision):
+    """At density ~47 every particle has ~200 partners within r_c, more than the
+    64 list slots: the force pass falls back to scanning the cells itself."""
+    w = I.tiny(3000, (4.0, 4.0, 4.0), 31, ntypes=2, spread=0.5)
+    s, p = make(M, w, precision)
+    f, rho = s.forces()
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
+    assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * o.rho.max()
+    assert rel_force_err(f, o.a) <= TOL[precision]
+    assert s.pair_count() > 64 * w.n
+    s.close()
+
+
+def test_list_and_scan_kernels_agree(M):
+    w = I.tiny(5000, (9.5, 9.0, 10.0), 32, ntypes=2, g=(0.02, 0, 0))
+    a = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 3)
+    b = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 3)
+    b.set_option(M.OPT_KERNELS, M.KERNELS_SCAN)
+    b.set_state(w.pos, w.vel)
+    a.step(20)
+    b.step(20)
+    xa, va, _, ra = a.state()
+    xb, vb, _, rb = b.state()
+    L = np.array(w.params.box)
+    # same pairs, same per-pair arithmetic; only the order of the FP32 sums differs
+    assert np.abs((xa - xb + L / 2) % L - L / 2).max() < 1e-5
+    assert np.abs(ra - rb).max() < 1e-4
+    assert a.pair_count() == b.pair_count()
+    a.close()
+    b.close()
