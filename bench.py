@@ -50,7 +50,7 @@ DESC = {
 }
 
 
-def make_workload(name: str, precision: int, seed: int):
+def make_workload(name: str, precision: int, seed: int, nvox: int = 256):
     from paper_1903_10134_gb300 import inputs as I
     if name == "bulk":
         return I.bulk(seed=seed, precision=precision)
@@ -59,7 +59,7 @@ def make_workload(name: str, precision: int, seed: int):
     if name == "slit":
         return I.slit(seed=seed, precision=precision)
     if name == "rock":
-        return I.rock(seed=seed, precision=precision)
+        return I.rock(nvox=nvox, seed=seed, precision=precision)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -172,7 +172,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    w = make_workload(args.workload, 0, seed=1)
+    w = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
     walls = _oracle_walls(w)
     o = O.Oracle(w.params.copy(), w.pos, w.vel, w.type, w.seed, use_cells=True, **walls)
     t0 = time.perf_counter()
@@ -220,7 +220,7 @@ def run_ours(args):
 
     dev = torch.cuda.current_device()
     prec = 0 if args.precision == "fp64" else 1
-    w = make_workload(args.workload, prec, seed=1 + rank)
+    w = make_workload(args.workload, prec, seed=1 + rank, nvox=args.nvox)
     stream = torch.cuda.Stream()
     s = mdpd.System.from_workload(w, stream=stream)
     n = s.n
@@ -322,7 +322,7 @@ def run_ours(args):
                 traffic = None
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            wc = make_workload(args.workload, 0, seed=1)
+            wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
             info = oracle_throughput(wc, args.cpu_seconds, max_steps=200)
             cpu = {"value": info["value"], "unit": "particle-steps/s", "cores": info["cores"],
                    "kind": "oracle",
@@ -334,6 +334,7 @@ def run_ours(args):
             "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": DESC[args.workload], "n": n,
+                       "nvox": args.nvox if args.workload == "rock" else None,
                        "precision": args.precision,
                        "l2": "flushed between timed steps" if flush else "working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -370,6 +371,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
+    ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
