@@ -223,6 +223,9 @@ def run_ours(args):
     w = make_workload(args.workload, prec, seed=1 + rank, nvox=args.nvox)
     stream = torch.cuda.Stream()
     s = mdpd.System.from_workload(w, stream=stream)
+    if args.kernels != "nlist":
+        s.set_option(mdpd.OPT_KERNELS, {"scan": mdpd.KERNELS_SCAN,
+                                        "nlist-thread": mdpd.KERNELS_NLIST_THREAD}[args.kernels])
     n = s.n
     working_set = n * (16 + 16 + 4 + 4 + 2 * 3 * 24 + 8)
     flush = working_set < 4 * L2_BYTES
@@ -335,7 +338,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": DESC[args.workload], "n": n,
                        "nvox": args.nvox if args.workload == "rock" else None,
-                       "precision": args.precision,
+                       "precision": args.precision, "kernels": args.kernels,
                        "l2": "flushed between timed steps" if flush else "working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_evals_per_s": value * pairs / 2 / n,
@@ -372,6 +375,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
+    ap.add_argument("--kernels", choices=("nlist", "nlist-thread", "scan"), default="nlist")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

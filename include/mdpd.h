@@ -175,14 +175,16 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *                      0: launch kernels one by one.
  *   MDPD_OPT_PROFILE   k > 0: record CUDA events around every kernel class of
  *                      the next steps (up to k steps); 0: off.
- *   MDPD_OPT_KERNELS   MDPD_KERNELS_NLIST (default): the density pass records
- *                      each mobile particle's partners within r_c and the
- *                      force pass walks that list; MDPD_KERNELS_SCAN: both
- *                      passes scan the 27 neighbour cells directly.  Same
- *                      results up to FP summation order.
+ *   MDPD_OPT_KERNELS   MDPD_KERNELS_NLIST (default): a warp-per-cell density
+ *                      pass records each mobile particle's partners within r_c
+ *                      and the force pass walks that list;
+ *                      MDPD_KERNELS_NLIST_THREAD: the same with a
+ *                      thread-per-particle density pass; MDPD_KERNELS_SCAN:
+ *                      both passes scan the 27 neighbour cells directly.
+ *                      Same results up to FP summation order.
  */
 enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3 };
-enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1 };
+enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1, MDPD_KERNELS_NLIST_THREAD = 2 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
 /* Kernel classes reported by mdpd_profile(). */

@@ -330,6 +330,9 @@ void enqueue_bin(mdpd_handle* h, bool gather_a)
 void enqueue_density(mdpd_handle* h)
 {
     if (h->kernels == MDPD_KERNELS_NLIST)
+        launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph,
+                            h->pos4, h->start, h->rho, h->nl, h->nl_count);
+    else if (h->kernels == MDPD_KERNELS_NLIST_THREAD)
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
                           h->cell_s, h->start, h->rho, h->nl, h->nl_count);
     else
@@ -339,7 +342,7 @@ void enqueue_density(mdpd_handle* h)
 
 void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 {
-    if (h->kernels == MDPD_KERNELS_NLIST)
+    if (h->kernels != MDPD_KERNELS_SCAN)
         launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
                         h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->nl, h->nl_count,
                         h->step, step_offset, master(h, h->cur), out, h->partials, h->status);
@@ -931,7 +934,8 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         h->use_graph = value != 0;
         return MDPD_OK;
     case MDPD_OPT_KERNELS:
-        if (value != MDPD_KERNELS_NLIST && value != MDPD_KERNELS_SCAN)
+        if (value != MDPD_KERNELS_NLIST && value != MDPD_KERNELS_SCAN &&
+            value != MDPD_KERNELS_NLIST_THREAD)
             return h->fail(MDPD_ERR_INVALID_ARG, "unknown kernel variant");
         CK(cudaStreamSynchronize(h->stream));
         h->kernels = (int)value;

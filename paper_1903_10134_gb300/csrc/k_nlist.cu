@@ -81,6 +81,148 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     for (uint32_t k = 0; k < m; ++k) nl[(int64_t)k * cap + s] = lst[k][threadIdx.x];
 }
 
+// Warp-cooperative density pass: one warp per home cell.  The 27 neighbour
+// cells' particles form one candidate sequence (a warp prefix sum over the
+// cells' counts); each lane takes one candidate per round of 32 and tests it
+// against up to DC_GROUP home particles broadcast from shared memory, so all
+// lanes run the same trip count.  Density terms accumulate per lane and are
+// summed with a fixed shuffle tree; partners within r_c of mobile home
+// particles are appended by warp ballot to per-particle lists staged in
+// shared memory, then written slot-major (nl[k * cap + i]).
+constexpr int DC_WARPS = 4;
+constexpr int DC_GROUP = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(DC_WARPS * 32)
+k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
+               const typename Vec4<T>::type* __restrict__ pos4,
+               const uint32_t* __restrict__ start, T* __restrict__ rho_out,
+               uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
+{
+    using V = typename Vec4<T>::type;
+    __shared__ V hpos[DC_WARPS][DC_GROUP];
+    __shared__ uint32_t pre[DC_WARPS][28];
+    __shared__ uint32_t cbase[DC_WARPS][27];
+    __shared__ uint32_t ccnt[DC_WARPS][DC_GROUP];
+    __shared__ uint32_t lst[DC_WARPS][NL_MAX][DC_GROUP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t c = (int64_t)blockIdx.x * DC_WARPS + w;
+    if (c >= ncell) return;                       // whole warp
+    const uint32_t hb = start[c], he = start[c + 1];
+    if (hb == he) return;                         // whole warp
+    int q0, q1, q2;
+    cell_coords((uint32_t)c, geo, q0, q1, q2);
+    uint32_t cb = 0, cn = 0;
+    if (lane < 27) {
+        const int x = neighbour_index(q0, lane % 3 - 1, geo.nc[0], geo.periodic[0]);
+        const int y = neighbour_index(q1, (lane / 3) % 3 - 1, geo.nc[1], geo.periodic[1]);
+        const int z = neighbour_index(q2, lane / 9 - 1, geo.nc[2], geo.periodic[2]);
+        if (x >= 0 && y >= 0 && z >= 0) {
+            const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
+            cb = start[nc];
+            cn = start[nc + 1] - cb;
+        }
+    }
+    uint32_t inc = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const uint32_t C = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane < 27) {
+        pre[w][lane] = inc - cn;
+        cbase[w][lane] = cb;
+    }
+    if (lane == 27) pre[w][27] = C;
+    __syncwarp();
+
+    const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
+    const T inv_rd = (T)(1.0 / ph.rd);
+    const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
+    const T hx = (T)geo.h[0], hy = (T)geo.h[1], hz = (T)geo.h[2];
+    const unsigned lt = (1u << lane) - 1u;
+
+    for (uint32_t g0 = hb; g0 < he; g0 += DC_GROUP) {
+        const int ng = (int)min((uint32_t)DC_GROUP, he - g0);
+        if (lane < ng) hpos[w][lane] = pos4[g0 + lane];
+        __syncwarp();
+        T acc[DC_GROUP];
+        uint32_t cnt[DC_GROUP];
+#pragma unroll
+        for (int i = 0; i < DC_GROUP; ++i) {
+            acc[i] = T(0);
+            cnt[i] = 0;
+        }
+        for (uint32_t t0 = 0; t0 < C; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const bool valid = t < C;
+            int lo = 0, hi = 27;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[w][mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t j = valid ? cbase[w][lo] + (t - pre[w][lo]) : hb;
+            const V pj = pos4[j];
+            const T shx = (T)(lo % 3 - 1) * hx;
+            const T shy = (T)((lo / 3) % 3 - 1) * hy;
+            const T shz = (T)(lo / 9 - 1) * hz;
+            const uint32_t entry = (j << 5) | (uint32_t)lo;
+#pragma unroll
+            for (int i = 0; i < DC_GROUP; ++i) {
+                if (i < ng) {
+                    const V pi = hpos[w][i];
+                    const T dx = pi.x - shx - pj.x;
+                    const T dy = pi.y - shy - pj.y;
+                    const T dz = pi.z - shz - pj.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    const bool other = valid && j != g0 + (uint32_t)i;
+                    if (other && r2 < rd2) {
+                        const T wr = T(1) - sqrt(r2) * inv_rd;
+                        acc[i] += cw * wr * wr;
+                    }
+                    const bool mob = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+                    const bool hc = other && mob && r2 < rc2 && r2 > T(0);
+                    const unsigned m = __ballot_sync(0xffffffffu, hc);
+                    if (m) {
+                        const uint32_t slot = cnt[i] + (uint32_t)__popc(m & lt);
+                        if (hc && slot < (uint32_t)NL_MAX) lst[w][slot][i] = entry;
+                        cnt[i] += (uint32_t)__popc(m);
+                    }
+                }
+            }
+        }
+        uint32_t maxc = 0;
+#pragma unroll
+        for (int i = 0; i < DC_GROUP; ++i) {
+            if (i < ng) {
+                T v = acc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    rho_out[g0 + i] = (ph.rho_self ? cw : T(0)) + v;
+                    nl_count[g0 + i] = cnt[i];
+                }
+                const uint32_t kept = cnt[i] < (uint32_t)NL_MAX ? cnt[i] : (uint32_t)NL_MAX;
+                if (lane == i) ccnt[w][i] = kept;
+                maxc = kept > maxc ? kept : maxc;
+            }
+        }
+        __syncwarp();
+        for (uint32_t e = lane; e < maxc * DC_GROUP; e += 32) {
+            const uint32_t slot = e / DC_GROUP, i = e % DC_GROUP;
+            if ((int)i < ng && slot < ccnt[w][i]) nl[(int64_t)slot * cap + g0 + i] = lst[w][slot][i];
+        }
+        __syncwarp();
+    }
+}
+
+// Force pass over the partner lists.  The particles of a block (128
+// consecutive in cell order) are first compacted so that the mobile ones sit
+// on the leading lanes (frozen wall particles need no force), then each of
+// those lanes walks its list with a two-stage software prefetch: list entries
+// two ahead, partner data one ahead.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(PAIR_BLOCK)
 k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
@@ -91,8 +233,11 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
            const uint64_t* __restrict__ step_ptr, int step_offset, Master m,
            double* __restrict__ out, double* __restrict__ partials, uint32_t* __restrict__ status)
 {
+    using V = typename Vec4<T>::type;
     __shared__ PairTables<T> tab;
     __shared__ T shift[27][3];
+    __shared__ int act[PAIR_BLOCK];
+    __shared__ int wsum[PAIR_BLOCK / 32];
     load_tables(tab, ph);
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
@@ -100,78 +245,105 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
         shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
     }
+    // compact the block's mobile particles onto the first lanes, in cell order
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
+    const bool mob0 = s0 < n && ((ph.frozen >> m.type[s0]) & 1u) == 0u;
+    const unsigned bal = __ballot_sync(0xffffffffu, mob0);
+    if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
+    int woff = 0, nact = 0;
+#pragma unroll
+    for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
+        woff += w < warp ? wsum[w] : 0;
+        nact += wsum[w];
+    }
+    if (mob0) act[woff + __popc(bal & ((1u << lane) - 1u))] = s0;
+    if (MODE == FM_EVAL && s0 < n && !mob0) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) out[k * cap + s0] = 0.0;
+    }
+    __syncthreads();
+
     const uint64_t step = *step_ptr + (uint64_t)step_offset;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
     double obs[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) obs[k] = 0.0;
-    if (s < n) {
+    if ((int)threadIdx.x < nact) {
+        const int s = act[threadIdx.x];
         const PairConst<T> c(ph);
-        const auto pi = pos4[s];
-        const auto vi = vel4[s];
+        const V pi = pos4[s];
+        const V vi = vel4[s];
         const T rho_i = rho[s];
         const uint32_t ti = unpack_u32(pi.w);
         const uint32_t id_i = unpack_u32(vi.w);
-        const bool mobile = ((ph.frozen >> ti) & 1u) == 0u;
+        const T* tA = tab.A + ti * 8;
+        const T* tB = tab.B + ti * 8;
+        const T* tG = tab.G + ti * 8;
+        const T* tS = tab.S + ti * 8;
         T f[3] = { T(0), T(0), T(0) };
         T W[6] = { T(0), T(0), T(0), T(0), T(0), T(0) };
         int npair = 0;
-        if (mobile) {
-            const T* tA = tab.A + ti * 8;
-            const T* tB = tab.B + ti * 8;
-            const T* tG = tab.G + ti * 8;
-            const T* tS = tab.S + ti * 8;
-            const uint32_t cnt = nl_count[s];
-            if (cnt <= (uint32_t)NL_MAX) {
-                for (uint32_t k = 0; k < cnt; ++k) {
-                    const uint32_t e = nl[(int64_t)k * cap + s];
-                    const uint32_t j = e >> 5, code = e & 31u;
-                    const auto pj = pos4[j];
-                    const T dx = pi.x - shift[code][0] - pj.x;
-                    const T dy = pi.y - shift[code][1] - pj.y;
-                    const T dz = pi.z - shift[code][2] - pj.z;
-                    const T r2 = dx * dx + dy * dy + dz * dz;
-                    const auto vj = vel4[j];
-                    pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i, rho[j],
-                              unpack_u32(pj.w), id_i, unpack_u32(vj.w), step, ph, f, W);
-                }
-                npair = (int)cnt;
-            } else {
-                int q0, q1, q2;
-                cell_coords(cell_s[s], geo, q0, q1, q2);
-                for (int oz = -1; oz <= 1; ++oz) {
-                    const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
-                    if (z < 0) continue;
-                    for (int oy = -1; oy <= 1; ++oy) {
-                        const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
-                        if (y < 0) continue;
-                        for (int ox = -1; ox <= 1; ++ox) {
-                            const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
-                            if (x < 0) continue;
-                            const int code = image_code(ox, oy, oz);
-                            const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
-                            const uint32_t b = start[nc], e = start[nc + 1];
-                            for (uint32_t j = b; j < e; ++j) {
-                                const auto pj = pos4[j];
-                                const T dx = pi.x - shift[code][0] - pj.x;
-                                const T dy = pi.y - shift[code][1] - pj.y;
-                                const T dz = pi.z - shift[code][2] - pj.z;
-                                const T r2 = dx * dx + dy * dy + dz * dz;
-                                if (r2 < c.rc2 && r2 > T(0)) {
-                                    const auto vj = vel4[j];
-                                    pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i,
-                                              rho[j], unpack_u32(pj.w), id_i, unpack_u32(vj.w),
-                                              step, ph, f, W);
-                                    ++npair;
-                                }
+        const uint32_t cnt = nl_count[s];
+        if (cnt <= (uint32_t)NL_MAX) {
+            uint32_t e0 = cnt > 0 ? nl[s] : 0u;
+            uint32_t e1 = cnt > 1 ? nl[cap + s] : 0u;
+            V pj = pos4[e0 >> 5];
+            V vj = vel4[e0 >> 5];
+            T rj = rho[e0 >> 5];
+            for (uint32_t k = 0; k < cnt; ++k) {
+                const uint32_t e2 = k + 2 < cnt ? nl[(int64_t)(k + 2) * cap + s] : 0u;
+                const V pn = pos4[e1 >> 5];
+                const V vn = vel4[e1 >> 5];
+                const T rn = rho[e1 >> 5];
+                const uint32_t code = e0 & 31u;
+                const T dx = pi.x - shift[code][0] - pj.x;
+                const T dy = pi.y - shift[code][1] - pj.y;
+                const T dz = pi.z - shift[code][2] - pj.z;
+                const T r2 = dx * dx + dy * dy + dz * dz;
+                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i, rj,
+                          unpack_u32(pj.w), id_i, unpack_u32(vj.w), step, ph, f, W);
+                e0 = e1;
+                e1 = e2;
+                pj = pn;
+                vj = vn;
+                rj = rn;
+            }
+            npair = (int)cnt;
+        } else {
+            int q0, q1, q2;
+            cell_coords(cell_s[s], geo, q0, q1, q2);
+            for (int oz = -1; oz <= 1; ++oz) {
+                const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
+                if (z < 0) continue;
+                for (int oy = -1; oy <= 1; ++oy) {
+                    const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
+                    if (y < 0) continue;
+                    for (int ox = -1; ox <= 1; ++ox) {
+                        const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
+                        if (x < 0) continue;
+                        const int code = image_code(ox, oy, oz);
+                        const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
+                        const uint32_t b = start[nc], e = start[nc + 1];
+                        for (uint32_t j = b; j < e; ++j) {
+                            const V pj = pos4[j];
+                            const T dx = pi.x - shift[code][0] - pj.x;
+                            const T dy = pi.y - shift[code][1] - pj.y;
+                            const T dz = pi.z - shift[code][2] - pj.z;
+                            const T r2 = dx * dx + dy * dy + dz * dz;
+                            if (r2 < c.rc2 && r2 > T(0)) {
+                                const V vj = vel4[j];
+                                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i,
+                                          rho[j], unpack_u32(pj.w), id_i, unpack_u32(vj.w),
+                                          step, ph, f, W);
+                                ++npair;
                             }
                         }
                     }
                 }
             }
         }
-        force_finish<T, MODE>(s, mobile, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
+        force_finish<T, MODE>(s, true, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     }
     block_obs_store(obs, partials);
 }
@@ -213,6 +385,21 @@ void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const
     else
         k_density_nl<float><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const float4*)pos4,
                                                        cell_s, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
+                         const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,
+                         void* rho, uint32_t* nl, uint32_t* nl_count)
+{
+    if (ncell <= 0) return;
+    const unsigned nb = (unsigned)((ncell + DC_WARPS - 1) / DC_WARPS);
+    if (precision == 0)
+        k_density_cell<double><<<nb, DC_WARPS * 32, 0, st>>>(ncell, cap, geo, ph, (const D4*)pos4,
+                                                             start, (double*)rho, nl, nl_count);
+    else
+        k_density_cell<float><<<nb, DC_WARPS * 32, 0, st>>>(ncell, cap, geo, ph,
+                                                            (const float4*)pos4, start,
+                                                            (float*)rho, nl, nl_count);
 }
 
 void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,

@@ -93,6 +93,10 @@ int force_num_blocks(int n);
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
                        const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count);
+// Warp-per-cell variant of launch_density_nl (same outputs).
+void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
+                         const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,
+                         void* rho, uint32_t* nl, uint32_t* nl_count);
 void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
                      const Geo& geo, const Phys& ph, const MaskDev& mk, const void* pos4,
                      const void* vel4, const void* rho, const uint32_t* cell_s,

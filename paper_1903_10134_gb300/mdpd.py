@@ -25,6 +25,7 @@ OPT_PROFILE = 2
 OPT_KERNELS = 3
 KERNELS_NLIST = 0
 KERNELS_SCAN = 1
+KERNELS_NLIST_THREAD = 2
 KCLASS = ("bin", "density", "force", "other")
 
 ERRORS = {

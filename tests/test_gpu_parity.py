@@ -49,7 +49,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernels", [0, 1])
+@pytest.mark.parametrize("kernels", [0, 1, 2])
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", CASES)
 def test_forces_and_density_match_oracle(M, case, precision, kernels):
