@@ -177,7 +177,7 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->slot, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->key, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->src, c * sizeof(uint32_t));
-    if (!rc) rc = dalloc(h, &h->partials, (size_t)force_num_blocks((int)c) * OBS_PARTIALS * sizeof(double));
+    if (!rc) rc = dalloc(h, &h->partials, (size_t)obs_num_partials((int)c) * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
     if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
@@ -354,7 +354,7 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 
 void enqueue_reduce(mdpd_handle* h, int advance)
 {
-    launch_reduce_obs(h->stream, h->partials, force_num_blocks((int)h->n), h->obs,
+    launch_reduce_obs(h->stream, h->partials, obs_num_partials((int)h->n), h->obs,
                       h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS, h->step, advance, 0.0);
 }
 

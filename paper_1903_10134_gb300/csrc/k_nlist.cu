@@ -24,14 +24,16 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
     return (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
 }
 
+// Thread-per-particle variant: each thread scans its 27 neighbour cells and
+// stores its partners straight to the slot-major list (no shared-memory
+// staging, so occupancy is set by registers alone).
 template <typename T>
-__global__ void __launch_bounds__(PAIR_BLOCK)
+__global__ void __launch_bounds__(PAIR_BLOCK, 12)
 k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
              const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
              const uint32_t* __restrict__ start, T* __restrict__ rho_out,
              uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
 {
-    __shared__ uint32_t lst[NL_MAX][PAIR_BLOCK];
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
@@ -62,13 +64,13 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                     const auto pj = pos4[j];
                     const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    if (j == (uint32_t)s) continue;
-                    if (r2 < rd2) {
+                    const bool other = j != (uint32_t)s;
+                    if (other && r2 < rd2) {
                         const T w = T(1) - sqrt(r2) * inv_rd;
                         acc += cw * w * w;
                     }
-                    if (mobile && r2 < rc2 && r2 > T(0)) {
-                        if (cnt < NL_MAX) lst[cnt][threadIdx.x] = (j << 5) | code;
+                    if (other && mobile && r2 < rc2 && r2 > T(0)) {
+                        if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
                         ++cnt;
                     }
                 }
@@ -77,8 +79,6 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     }
     rho_out[s] = acc;
     nl_count[s] = cnt;
-    const uint32_t m = cnt < NL_MAX ? cnt : NL_MAX;
-    for (uint32_t k = 0; k < m; ++k) nl[(int64_t)k * cap + s] = lst[k][threadIdx.x];
 }
 
 // Warp-cooperative density pass: one warp per home cell.  The 27 neighbour
@@ -345,7 +345,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         }
         force_finish<T, MODE>(s, true, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     }
-    block_obs_store(obs, partials);
+    warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
 template <typename T>

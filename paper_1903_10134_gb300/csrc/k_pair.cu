@@ -138,7 +138,7 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         }
         force_finish<T, MODE>(s, mobile, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     }
-    block_obs_store(obs, partials);
+    warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
 __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, Master m,
@@ -248,6 +248,8 @@ void launch_force_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const G
 }  // namespace
 
 int force_num_blocks(int n) { return n > 0 ? (n + PAIR_BLOCK - 1) / PAIR_BLOCK : 1; }
+
+int obs_num_partials(int n) { return force_num_blocks(n) * (PAIR_BLOCK / 32); }
 
 void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const Phys& ph,
                     const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho)

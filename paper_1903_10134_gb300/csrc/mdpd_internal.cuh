@@ -62,7 +62,7 @@ enum ForceMode : int {
                     // drift and reflection
 };
 
-constexpr int OBS_PARTIALS = 16;   // doubles per block in the reduction
+constexpr int OBS_PARTIALS = 16;   // observable slots per partial (14 used)
 
 // ---- launchers (binning / scan) -------------------------------------------
 void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, const Geo& geo,
@@ -88,6 +88,8 @@ void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t
                   const uint32_t* start, const uint64_t* step_ptr, int step_offset,
                   const Master& m, double* out, double* partials, uint32_t* status);
 int force_num_blocks(int n);
+// Number of per-warp observable partials the force pass writes for n particles.
+int obs_num_partials(int n);
 // Density pass that also writes the force partners of mobile particles
 // (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,

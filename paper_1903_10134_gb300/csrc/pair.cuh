@@ -188,25 +188,38 @@ __device__ __forceinline__ void force_finish(int s, bool mobile, const T (&f)[3]
     if (st) atomicOr(status, st);
 }
 
-// Deterministic block sum of NOBS doubles into partials[k * gridDim.x + blockIdx.x]
-// (all threads of the block must call it).
-__device__ __forceinline__ void block_obs_store(double (&o)[NOBS], double* __restrict__ partials)
+// Per-warp partial sums of the observables, written to
+// partials[k * nparts + global warp index] with no block-wide barrier, so a
+// warp that finishes early does not hold its block.  FP64 arithmetic is slow
+// on this part, so the FP64 values are transposed through shared memory and
+// summed serially by a few lanes (16 values per lane, then one combining
+// add) instead of a shuffle tree in which every lane adds at every level;
+// the two integer counts use the warp integer reduction.  The order of the
+// additions is fixed, so the result is reproducible.
+constexpr int NOBS_F = 12;   // momentum 3, sum v^2 3, virial 6
+
+__device__ __forceinline__ void warp_obs_store(const double (&o)[NOBS], double* __restrict__ partials,
+                                               int64_t nparts)
 {
-    __shared__ double sh[PAIR_BLOCK / 32][NOBS];
+    __shared__ double sh[PAIR_BLOCK / 32][NOBS_F][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) {
-        double v = o[k];
+    for (int k = 0; k < NOBS_F; ++k) sh[warp][k][lane] = o[k];
+    const unsigned nm = __reduce_add_sync(0xffffffffu, (unsigned)o[12]);
+    const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)o[13]);
+    __syncwarp();
+    const int k = lane & 15, half = lane >> 4;
+    double v = 0.0;
+    if (k < NOBS_F) {
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[warp][k] = v;
+        for (int l = 0; l < 16; ++l) v += sh[warp][k][16 * half + l];
     }
-    __syncthreads();
-    if (threadIdx.x < NOBS) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < PAIR_BLOCK / 32; ++w) v += sh[w][threadIdx.x];
-        partials[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    v += __shfl_down_sync(0xffffffffu, v, 16);
+    const int64_t gw = (int64_t)blockIdx.x * (PAIR_BLOCK / 32) + warp;
+    if (lane < NOBS_F) partials[(int64_t)lane * nparts + gw] = v;
+    if (lane == 0) {
+        partials[(int64_t)12 * nparts + gw] = (double)nm;
+        partials[(int64_t)13 * nparts + gw] = (double)np;
     }
 }
 
