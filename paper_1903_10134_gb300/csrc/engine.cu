@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "mdpd_internal.cuh"
@@ -60,6 +61,8 @@ struct mdpd_handle {
     uint32_t* status = nullptr;
     uint64_t* step = nullptr;
     double* partials = nullptr;
+    double* red_l1 = nullptr;        // level-one partials of the reduction
+    unsigned* red_ticket = nullptr;  // last-block ticket of the reduction
     double* obs = nullptr;       // MDPD_NUM_OBS current, then MDPD_NUM_OBS sums, then count
     double* fout = nullptr;      // 3 * cap staging / force output
     uint8_t* type_by_id = nullptr;
@@ -150,6 +153,7 @@ void free_particles(mdpd_handle* h)
     dfree(h->key);
     dfree(h->src);
     dfree(h->partials);
+    dfree(h->red_l1);
     dfree(h->fout);
     dfree(h->type_by_id);
     dfree(h->nl);
@@ -178,12 +182,40 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->key, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->src, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->partials, (size_t)obs_num_partials((int)c) * OBS_PARTIALS * sizeof(double));
+    if (!rc) rc = dalloc(h, &h->red_l1, (size_t)(reduce_l1_blocks(obs_num_partials((int)c)) + 1) * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
     if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->nl_count, c * sizeof(uint32_t));
     if (!rc) h->cap = (int64_t)c;
     return rc;
+}
+
+// Exchange every per-particle array (and the capacity) of two handles.
+void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
+{
+    for (int k = 0; k < 2; ++k) {
+        std::swap(a->x[k], b->x[k]);
+        std::swap(a->v[k], b->v[k]);
+        std::swap(a->a[k], b->a[k]);
+        std::swap(a->id[k], b->id[k]);
+        std::swap(a->type[k], b->type[k]);
+    }
+    std::swap(a->pos4, b->pos4);
+    std::swap(a->vel4, b->vel4);
+    std::swap(a->rho, b->rho);
+    std::swap(a->cell_s, b->cell_s);
+    std::swap(a->cellof, b->cellof);
+    std::swap(a->slot, b->slot);
+    std::swap(a->key, b->key);
+    std::swap(a->src, b->src);
+    std::swap(a->partials, b->partials);
+    std::swap(a->red_l1, b->red_l1);
+    std::swap(a->fout, b->fout);
+    std::swap(a->type_by_id, b->type_by_id);
+    std::swap(a->nl, b->nl);
+    std::swap(a->nl_count, b->nl_count);
+    std::swap(a->cap, b->cap);
 }
 
 void destroy_graphs(mdpd_handle* h)
@@ -354,8 +386,9 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 
 void enqueue_reduce(mdpd_handle* h, int advance)
 {
-    launch_reduce_obs(h->stream, h->partials, obs_num_partials((int)h->n), h->obs,
-                      h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS, h->step, advance, 0.0);
+    launch_reduce_obs(h->stream, h->partials, obs_num_partials((int)h->n), h->red_l1,
+                      h->red_ticket, h->obs, h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS,
+                      h->step, advance);
 }
 
 // One velocity-Verlet step after the first half-kick and drift:
@@ -548,6 +581,7 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
         (rc = dalloc(h, &h->scan_tmp, (size_t)(nb + 1) * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->status, sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->step, sizeof(uint64_t))) ||
+        (rc = dalloc(h, &h->red_ticket, sizeof(unsigned))) ||
         (rc = dalloc(h, &h->obs, (2 * MDPD_NUM_OBS + 2) * sizeof(double))))
         return bail(rc);
     for (int k = 0; k < EV_PER_STEP; ++k)
@@ -563,6 +597,7 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
     const cudaMemcpyKind kind = device_inputs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     bool ok = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), st) == cudaSuccess &&
               cudaMemsetAsync(h->step, 0, sizeof(uint64_t), st) == cudaSuccess &&
+              cudaMemsetAsync(h->red_ticket, 0, sizeof(unsigned), st) == cudaSuccess &&
               cudaMemsetAsync(h->obs, 0, (2 * MDPD_NUM_OBS + 2) * sizeof(double), st) == cudaSuccess;
     if (ok && n > 0)
         ok = cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), kind, st) == cudaSuccess &&
@@ -672,41 +707,18 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
         dfree(bits);
         return h->fail(MDPD_ERR_INVALID_ARG, "too many particles with walls");
     }
-    // move the state into arrays of the new capacity
-    mdpd_handle tmpH;       // holds the old arrays while the new ones are filled
-    tmpH.precision = h->precision;
-    for (int k = 0; k < 2; ++k) {
-        tmpH.x[k] = h->x[k]; tmpH.v[k] = h->v[k]; tmpH.a[k] = h->a[k];
-        tmpH.id[k] = h->id[k]; tmpH.type[k] = h->type[k];
-        h->x[k] = h->v[k] = h->a[k] = nullptr; h->id[k] = nullptr; h->type[k] = nullptr;
-    }
-    tmpH.pos4 = h->pos4; tmpH.vel4 = h->vel4; tmpH.rho = h->rho; tmpH.cell_s = h->cell_s;
-    tmpH.cellof = h->cellof; tmpH.slot = h->slot; tmpH.key = h->key; tmpH.src = h->src;
-    tmpH.partials = h->partials; tmpH.fout = h->fout; tmpH.type_by_id = h->type_by_id;
-    h->pos4 = h->vel4 = h->rho = nullptr;
-    h->cell_s = h->cellof = h->slot = h->key = h->src = nullptr;
-    h->partials = h->fout = nullptr;
-    h->type_by_id = nullptr;
-    const int64_t old_cap = h->cap;
-    if ((rc = alloc_particles(h, n_new))) {
-        free_particles(h);
-        // restore the old arrays
-        for (int k = 0; k < 2; ++k) {
-            h->x[k] = tmpH.x[k]; h->v[k] = tmpH.v[k]; h->a[k] = tmpH.a[k];
-            h->id[k] = tmpH.id[k]; h->type[k] = tmpH.type[k];
-            tmpH.x[k] = tmpH.v[k] = tmpH.a[k] = nullptr; tmpH.id[k] = nullptr; tmpH.type[k] = nullptr;
-        }
-        h->pos4 = tmpH.pos4; h->vel4 = tmpH.vel4; h->rho = tmpH.rho; h->cell_s = tmpH.cell_s;
-        h->cellof = tmpH.cellof; h->slot = tmpH.slot; h->key = tmpH.key; h->src = tmpH.src;
-        h->partials = tmpH.partials; h->fout = tmpH.fout; h->type_by_id = tmpH.type_by_id;
-        tmpH.pos4 = tmpH.vel4 = tmpH.rho = nullptr;
-        tmpH.cell_s = tmpH.cellof = tmpH.slot = tmpH.key = tmpH.src = nullptr;
-        tmpH.partials = tmpH.fout = nullptr; tmpH.type_by_id = nullptr;
-        h->cap = old_cap;
+    // fill arrays of the new capacity in a scratch handle, then swap them in
+    mdpd_handle nh;
+    nh.precision = h->precision;
+    if ((rc = alloc_particles(&nh, n_new))) {
+        free_particles(&nh);
         cleanup();
         dfree(bits);
-        return rc;
+        return h->fail(rc, nh.err);
     }
+    const int64_t old_cap = h->cap;
+    swap_particle_arrays(h, &nh);     // h: new arrays, nh: old arrays (old_cap)
+    mdpd_handle& tmpH = nh;
     const int c = h->cur;
     ok = true;
     for (int k = 0; k < 3 && ok; ++k) {
@@ -1000,6 +1012,7 @@ void mdpd_destroy(mdpd_handle* h)
     dfree(h->scan_tmp);
     dfree(h->status);
     dfree(h->step);
+    dfree(h->red_ticket);
     dfree(h->obs);
     dfree(h->mask_bits);
     for (auto& e : h->tev)

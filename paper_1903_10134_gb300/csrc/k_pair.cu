@@ -162,24 +162,34 @@ __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, M
     if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) atomicOr(status, ST_NONFINITE);
 }
 
-// One block: fixed-order sum of the per-block partials (laid out [k][block]),
-// then the derived observables; with `advance` the step counter moves on and
-// the running sums accumulate.
-constexpr int RED_THREADS = 512;
+// Final reduction of the observables, one launch in two levels: block b sums
+// the per-warp partials [b * RED_CHUNK, (b + 1) * RED_CHUNK) (threads take
+// fixed strided subsets, then a fixed shuffle tree), writes its level-one
+// partial, and counts itself done on a global ticket; the block that takes the
+// last ticket sums the level-one partials in block order, derives the
+// observables, accumulates the running sums, advances the step counter when
+// asked, and resets the ticket for the next launch.  Every addition happens
+// in a fixed order, so the result is reproducible.
+constexpr int RED_THREADS = 256;
+constexpr int RED_CHUNK = 2048;
 
 __global__ void __launch_bounds__(RED_THREADS)
-k_reduce_obs(const double* __restrict__ partials, int nblocks, double* __restrict__ obs,
+k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict__ l1,
+             unsigned* __restrict__ ticket, double* __restrict__ obs,
              double* __restrict__ obs_sum, double* __restrict__ obs_count,
              uint64_t* __restrict__ step_ptr, int advance)
 {
     __shared__ double sh[RED_THREADS / 32][NOBS];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int b0 = blockIdx.x * RED_CHUNK;
+    const int b1 = min(nparts, b0 + RED_CHUNK);
     double acc[NOBS];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += RED_THREADS)
+    for (int b = b0 + threadIdx.x; b < b1; b += RED_THREADS)
 #pragma unroll
-        for (int k = 0; k < NOBS; ++k) acc[k] += partials[(int64_t)k * nblocks + b];
+        for (int k = 0; k < NOBS; ++k) acc[k] += partials[(int64_t)k * nparts + b];
 #pragma unroll
     for (int k = 0; k < NOBS; ++k) {
         double v = acc[k];
@@ -188,12 +198,25 @@ k_reduce_obs(const double* __restrict__ partials, int nblocks, double* __restric
         if (lane == 0) sh[warp][k] = v;
     }
     __syncthreads();
+    if (threadIdx.x < NOBS) {
+        double v = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; ++w) v += sh[w][threadIdx.x];
+        l1[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x < NOBS) {
+        double v = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&l1[(int64_t)threadIdx.x * gridDim.x + b]);
+        sh[0][threadIdx.x] = v;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        double t[NOBS];
-        for (int k = 0; k < NOBS; ++k) {
-            t[k] = 0.0;
-            for (int w = 0; w < RED_THREADS / 32; ++w) t[k] += sh[w][k];
-        }
+        const double* t = sh[0];
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
         double o[MDPD_NUM_OBS];
         for (int k = 0; k < 3; ++k) o[k] = t[k];
@@ -211,6 +234,7 @@ k_reduce_obs(const double* __restrict__ partials, int nblocks, double* __restric
             *obs_count += 1.0;
             *step_ptr = step;
         }
+        *ticket = 0u;
     }
 }
 
@@ -285,12 +309,15 @@ void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, cons
     k_kick_drift<<<(n + 255) / 256, 256, 0, st>>>(n, cap, geo, ph, mk, m, status);
 }
 
-void launch_reduce_obs(cudaStream_t st, const double* partials, int nblocks, double* obs,
-                       double* obs_sum, double* obs_count, uint64_t* step_ptr, int advance,
-                       double)
+int reduce_l1_blocks(int nparts) { return (nparts + RED_CHUNK - 1) / RED_CHUNK; }
+
+void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
+                       unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
+                       uint64_t* step_ptr, int advance)
 {
-    k_reduce_obs<<<1, RED_THREADS, 0, st>>>(partials, nblocks, obs, obs_sum, obs_count, step_ptr,
-                                    advance);
+    const int nb = reduce_l1_blocks(nparts) > 0 ? reduce_l1_blocks(nparts) : 1;
+    k_reduce_obs<<<nb, RED_THREADS, 0, st>>>(partials, nparts, l1, ticket, obs, obs_sum,
+                                             obs_count, step_ptr, advance);
 }
 
 }  // namespace mdpd

@@ -108,9 +108,13 @@ void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int6
 constexpr int NL_SLOTS = 64;      // must equal NL_MAX of the kernels
 void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                        const MaskDev& mk, const Master& m, uint32_t* status);
-void launch_reduce_obs(cudaStream_t st, const double* partials, int nblocks, double* obs,
-                       double* obs_sum, double* obs_count, uint64_t* step_ptr, int advance,
-                       double kT_dof_n);
+// Level-one blocks of the observable reduction for nparts partials.
+int reduce_l1_blocks(int nparts);
+// Two-level reduction of the per-warp partials (l1: NOBS * reduce_l1_blocks
+// doubles; ticket: one zero-initialised counter, left at zero).
+void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
+                       unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
+                       uint64_t* step_ptr, int advance);
 
 // ---- launchers (walls) -----------------------------------------------------
 void launch_mask_pack(cudaStream_t st, const uint8_t* mask, int64_t nvox, uint32_t* bits);
