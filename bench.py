@@ -243,7 +243,7 @@ def run_ours(args):
     pairs = s.pair_count()
 
     K = args.steps
-    s.set_option(mdpd.OPT_PROFILE, K)
+    s.set_option(mdpd.OPT_PROFILE, 0 if args.no_profile else K)
     clocks = ClockSampler(dev) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
@@ -371,6 +371,8 @@ def main():
     ap.add_argument("--workload", choices=tuple(DESC), default="slab")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-profile", action="store_true",
+                    help="no per-kernel events in the timed region (no roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
