@@ -223,7 +223,12 @@ def run_ours(args):
     w = make_workload(args.workload, prec, seed=1 + rank, nvox=args.nvox)
     stream = torch.cuda.Stream()
     s = mdpd.System.from_workload(w, stream=stream)
-    if args.kernels != "nlist":
+    tuned = None
+    if args.kernels == "auto":
+        chosen, tms = s.autotune()
+        tuned = {"chosen": {mdpd.KERNELS_NLIST: "nlist", mdpd.KERNELS_NLIST_THREAD: "nlist-thread"}[chosen],
+                 "density_ms": {"nlist": tms[0], "nlist-thread": tms[1]}}
+    elif args.kernels != "nlist":
         s.set_option(mdpd.OPT_KERNELS, {"scan": mdpd.KERNELS_SCAN,
                                         "nlist-thread": mdpd.KERNELS_NLIST_THREAD}[args.kernels])
     n = s.n
@@ -244,6 +249,7 @@ def run_ours(args):
 
     K = args.steps
     s.set_option(mdpd.OPT_PROFILE, 0 if args.no_profile else K)
+    s.set_option(mdpd.OPT_PROFILE_EVERY, args.profile_every)
     clocks = ClockSampler(dev) if rank == 0 else None
     if world > 1:
         torch.distributed.barrier()
@@ -338,7 +344,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": DESC[args.workload], "n": n,
                        "nvox": args.nvox if args.workload == "rock" else None,
-                       "precision": args.precision, "kernels": args.kernels,
+                       "precision": args.precision, "kernels": args.kernels, "autotune": tuned,
                        "l2": "flushed between timed steps" if flush else "working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_evals_per_s": value * pairs / 2 / n,
@@ -377,7 +383,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
-    ap.add_argument("--kernels", choices=("nlist", "nlist-thread", "scan"), default="nlist")
+    ap.add_argument("--kernels", choices=("auto", "nlist", "nlist-thread", "scan"), default="auto")
+    ap.add_argument("--profile-every", type=int, default=10,
+                    help="record per-kernel events on every k-th timed step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

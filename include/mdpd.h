@@ -182,8 +182,12 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *                      thread-per-particle density pass; MDPD_KERNELS_SCAN:
  *                      both passes scan the 27 neighbour cells directly.
  *                      Same results up to FP summation order.
+ *   MDPD_OPT_PROFILE_EVERY  m >= 1: with MDPD_OPT_PROFILE on, record the events
+ *                      on every m-th step only (default 1), which keeps their
+ *                      cost out of most steps.
  */
-enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3 };
+enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3,
+       MDPD_OPT_PROFILE_EVERY = 4 };
 enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1, MDPD_KERNELS_NLIST_THREAD = 2 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
@@ -195,6 +199,12 @@ enum { MDPD_K_BIN = 0, MDPD_K_DENSITY = 1, MDPD_K_FORCE = 2, MDPD_K_OTHER = 3,
  * recorded; clears the record.  Synchronises. */
 int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps,
                  int64_t* launches);
+
+/* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD)
+ * on the current state, reps launches each, and keep the faster one.  The
+ * trajectory is not advanced.  chosen (may be NULL) receives the variant, ms
+ * (may be NULL, 2 doubles) the mean time of each.  Synchronises. */
+int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms);
 
 /* Grid of the cell lattice (cells per axis) and the kernel launches one step
  * issues. */

@@ -81,6 +81,7 @@ struct mdpd_handle {
 
     // profiling ring
     int64_t prof_cap = 0, prof_used = 0;
+    int64_t prof_every = 1, prof_tick = 0;   // record events on every prof_every-th step
     std::vector<cudaEvent_t> prof_ev;
     int64_t prof_launches = 0;
 
@@ -461,6 +462,7 @@ int capture_step(mdpd_handle* h, int prof, int mode, int cur)
 cudaEvent_t* next_prof_events(mdpd_handle* h)
 {
     if (h->prof_used >= h->prof_cap) return nullptr;
+    if (h->prof_every > 1 && (h->prof_tick++ % h->prof_every) != 0) return nullptr;
     cudaEvent_t* evs = &h->prof_ev[(size_t)h->prof_used * EV_PER_STEP];
     ++h->prof_used;
     return evs;
@@ -752,6 +754,11 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
         h->mk.origin[k] = origin[k];
     }
     h->mk.voxel = voxel;
+    h->mk.inv_voxel = 1.0 / voxel;
+    {
+        int ex = 0;
+        h->mk.inv_voxel_exact = std::frexp(voxel, &ex) == 0.5 ? 1 : 0;
+    }
     h->walls_set = true;
     destroy_graphs(h);
     if ((rc = evaluate(h, nullptr, false))) return rc;
@@ -965,8 +972,14 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         h->prof_cap = value;
         h->prof_used = 0;
         h->prof_launches = 0;
+        h->prof_tick = 0;
         return MDPD_OK;
     }
+    case MDPD_OPT_PROFILE_EVERY:
+        if (value < 1) return h->fail(MDPD_ERR_INVALID_ARG, "profile interval must be >= 1");
+        h->prof_every = value;
+        h->prof_tick = 0;
+        return MDPD_OK;
     default:
         return h->fail(MDPD_ERR_INVALID_ARG, "unknown option");
     }
@@ -990,6 +1003,48 @@ int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps, int
     h->prof_used = 0;
     h->prof_launches = 0;
     return MDPD_OK;
+}
+
+int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (reps < 1) reps = 5;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    const int variants[2] = { MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = h->kernels;
+    double best_ms = 1e300;
+    for (int v = 0; v < 2; ++v) {
+        h->kernels = variants[v];
+        enqueue_bin(h, true);                 // same positions: same order, state kept
+        enqueue_density(h);                   // warm-up
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps; ++r) enqueue_density(h);
+        cudaEventRecord(e1, h->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return h->fail(MDPD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
+        }
+        if (ms) ms[v] = t / reps;
+        if (t < best_ms) {
+            best_ms = t;
+            best = variants[v];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->kernels = best;
+    destroy_graphs(h);
+    enqueue_density(h);                       // rho and lists from the chosen variant
+    if (chosen) *chosen = best;
+    return sync_check(h);
 }
 
 int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_step)

@@ -66,7 +66,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     const bool other = j != (uint32_t)s;
                     if (other && r2 < rd2) {
-                        const T w = T(1) - sqrt(r2) * inv_rd;
+                        const T w = T(1) - sqrt_t(r2) * inv_rd;
                         acc += cw * w * w;
                     }
                     if (other && mobile && r2 < rc2 && r2 > T(0)) {
@@ -106,12 +106,10 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
     __shared__ uint32_t ccnt[DC_WARPS][DC_GROUP];
     __shared__ uint32_t lst[DC_WARPS][NL_MAX][DC_GROUP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t nwarps = (int64_t)gridDim.x * DC_WARPS;
-    // grid-stride over cells: a warp takes cells w0, w0 + nwarps, ... and skips
-    // empty ones at the cost of two loads
-    for (int64_t c = (int64_t)blockIdx.x * DC_WARPS + w; c < ncell; c += nwarps) {
+    const int64_t c = (int64_t)blockIdx.x * DC_WARPS + w;
+    if (c >= ncell) return;                       // whole warp
     const uint32_t hb = start[c], he = start[c + 1];
-    if (hb == he) continue;                       // whole warp
+    if (hb == he) return;                         // whole warp
     int q0, q1, q2;
     cell_coords((uint32_t)c, geo, q0, q1, q2);
     uint32_t cb = 0, cn = 0;
@@ -181,7 +179,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     const bool other = valid && j != g0 + (uint32_t)i;
                     if (other && r2 < rd2) {
-                        const T wr = T(1) - sqrt(r2) * inv_rd;
+                        const T wr = T(1) - sqrt_t(r2) * inv_rd;
                         acc[i] += cw * wr * wr;
                     }
                     const bool mob = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
@@ -217,8 +215,6 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
             if ((int)i < ng && slot < ccnt[w][i]) nl[(int64_t)slot * cap + g0 + i] = lst[w][slot][i];
         }
         __syncwarp();
-    }
-    __syncwarp();
     }
 }
 
@@ -396,15 +392,7 @@ void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t 
                          void* rho, uint32_t* nl, uint32_t* nl_count)
 {
     if (ncell <= 0) return;
-    static int nsm = 0;                 // SM count of the device (same on every GB300)
-    if (nsm <= 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
-            nsm = 152;
-    }
-    const int64_t want = (ncell + DC_WARPS - 1) / DC_WARPS;
-    const unsigned nb = (unsigned)(want < (int64_t)nsm * 8 ? want : (int64_t)nsm * 8);
+    const unsigned nb = (unsigned)((ncell + DC_WARPS - 1) / DC_WARPS);
     if (precision == 0)
         k_density_cell<double><<<nb, DC_WARPS * 32, 0, st>>>(ncell, cap, geo, ph, (const D4*)pos4,
                                                              start, (double*)rho, nl, nl_count);

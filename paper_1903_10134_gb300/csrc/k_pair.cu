@@ -162,16 +162,18 @@ __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, M
     if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) atomicOr(status, ST_NONFINITE);
 }
 
-// Final reduction of the observables, one launch in two levels: block b sums
-// the per-warp partials [b * RED_CHUNK, (b + 1) * RED_CHUNK) (threads take
-// fixed strided subsets, then a fixed shuffle tree), writes its level-one
-// partial, and counts itself done on a global ticket; the block that takes the
-// last ticket sums the level-one partials in block order, derives the
-// observables, accumulates the running sums, advances the step counter when
-// asked, and resets the ticket for the next launch.  Every addition happens
-// in a fixed order, so the result is reproducible.
-constexpr int RED_THREADS = 256;
-constexpr int RED_CHUNK = 2048;
+// Final reduction of the observables, one launch in two levels.  FP64 adds
+// run at a small fraction of the FP32 rate on this part, so the sums are laid
+// out to do few of them: block b takes the per-warp partials
+// [b * RED_CHUNK, (b + 1) * RED_CHUNK), one per thread, transposes them
+// through shared memory, and 16 threads per observable add 16 values each
+// before one thread adds those 16 results; the block writes its level-one
+// partial and takes a ticket.  The block holding the last ticket adds the
+// level-one partials in block order, derives the observables, accumulates the
+// running sums, advances the step counter when asked and resets the ticket.
+// Every addition happens in a fixed order, so the result is reproducible.
+constexpr int RED_CHUNK = 256;
+constexpr int RED_THREADS = RED_CHUNK;
 
 __global__ void __launch_bounds__(RED_THREADS)
 k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict__ l1,
@@ -179,28 +181,26 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
              double* __restrict__ obs_sum, double* __restrict__ obs_count,
              uint64_t* __restrict__ step_ptr, int advance)
 {
-    __shared__ double sh[RED_THREADS / 32][NOBS];
+    __shared__ double sh[NOBS][RED_CHUNK + 1];
+    __shared__ double s16[NOBS][17];
     __shared__ bool last;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int b0 = blockIdx.x * RED_CHUNK;
-    const int b1 = min(nparts, b0 + RED_CHUNK);
-    double acc[NOBS];
+    const int b = blockIdx.x * RED_CHUNK + threadIdx.x;
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) acc[k] = 0.0;
-    for (int b = b0 + threadIdx.x; b < b1; b += RED_THREADS)
+    for (int k = 0; k < NOBS; ++k)
+        sh[k][threadIdx.x] = b < nparts ? partials[(int64_t)k * nparts + b] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < NOBS * 16) {
+        const int k = threadIdx.x >> 4, part = threadIdx.x & 15;
+        double v = 0.0;
 #pragma unroll
-        for (int k = 0; k < NOBS; ++k) acc[k] += partials[(int64_t)k * nparts + b];
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) {
-        double v = acc[k];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0) sh[warp][k] = v;
+        for (int l = 0; l < RED_CHUNK / 16; ++l) v += sh[k][part * (RED_CHUNK / 16) + l];
+        s16[k][part] = v;
     }
     __syncthreads();
     if (threadIdx.x < NOBS) {
         double v = 0.0;
-        for (int w = 0; w < RED_THREADS / 32; ++w) v += sh[w][threadIdx.x];
+#pragma unroll
+        for (int l = 0; l < 16; ++l) v += s16[threadIdx.x][l];
         l1[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
     }
     __threadfence();
@@ -211,12 +211,13 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
     __threadfence();
     if (threadIdx.x < NOBS) {
         double v = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(&l1[(int64_t)threadIdx.x * gridDim.x + b]);
-        sh[0][threadIdx.x] = v;
+        for (unsigned q = 0; q < gridDim.x; ++q) v += __ldcg(&l1[(int64_t)threadIdx.x * gridDim.x + q]);
+        s16[threadIdx.x][16] = v;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const double* t = sh[0];
+        double t[NOBS];
+        for (int k = 0; k < NOBS; ++k) t[k] = s16[k][16];
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
         double o[MDPD_NUM_OBS];
         for (int k = 0; k < 3; ++k) o[k] = t[k];

@@ -42,6 +42,8 @@ struct MaskDev {
     const uint32_t* bits;
     int dim[3];
     double voxel;
+    double inv_voxel;      // 1 / voxel
+    int inv_voxel_exact;   // voxel is a power of two: t * inv_voxel == t / voxel
     double origin[3];
 };
 

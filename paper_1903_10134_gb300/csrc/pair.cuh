@@ -16,6 +16,10 @@ constexpr int NL_MAX = NL_SLOTS;   // neighbour-list slots per particle (more: d
 
 __device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
+// r from r^2 (> 0) for the density weight: FP32 through the hardware reciprocal
+// square root (about 2 ulp), FP64 correctly rounded.
+__device__ __forceinline__ float sqrt_t(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T xi_of(U4 w, int dist)
@@ -109,7 +113,10 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
         int64_t q[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const double f = floor(__ddiv_rn(__dsub_rn(xn[k], mk.origin[k]), mk.voxel));
+            const double t = __dsub_rn(xn[k], mk.origin[k]);
+            // for a power-of-two voxel t * (1/voxel) is exactly t / voxel
+            const double f = floor(mk.inv_voxel_exact ? __dmul_rn(t, mk.inv_voxel)
+                                                      : __ddiv_rn(t, mk.voxel));
             if (!(f >= 0.0) || f >= (double)mk.dim[k]) inside = false;
             q[k] = inside ? (int64_t)f : 0;
         }

@@ -23,6 +23,7 @@ NUM_OBS = 16
 OPT_GRAPH = 1
 OPT_PROFILE = 2
 OPT_KERNELS = 3
+OPT_PROFILE_EVERY = 4
 KERNELS_NLIST = 0
 KERNELS_SCAN = 1
 KERNELS_NLIST_THREAD = 2
@@ -91,7 +92,8 @@ SYMBOLS = (
     "mdpd_set_state", "mdpd_set_state_dev", "mdpd_forces", "mdpd_forces_dev",
     "mdpd_observables", "mdpd_observables_mean", "mdpd_pair_count", "mdpd_set_option",
     "mdpd_profile",
-    "mdpd_describe", "mdpd_density_noalloc", "mdpd_destroy", "mdpd_last_error",
+    "mdpd_describe", "mdpd_autotune", "mdpd_density_noalloc", "mdpd_destroy",
+    "mdpd_last_error",
 )
 
 
@@ -129,6 +131,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_profile.argtypes = [P, P, C.POINTER(i64), C.POINTER(i64)]
     L.mdpd_describe.argtypes = [P, P, C.POINTER(i32)]
     L.mdpd_density_noalloc.argtypes = [P, i64, P, P, P]
+    L.mdpd_autotune.argtypes = [P, i32, C.POINTER(i32), P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -307,6 +310,15 @@ def mdpd_describe(h):
     return nc.tolist(), int(lps.value)
 
 
+def mdpd_autotune(h, reps: int = 5):
+    """Pick the faster density-pass variant on the current state; returns
+    (chosen variant, [ms of each variant])."""
+    chosen = C.c_int32()
+    ms = np.zeros(2)
+    _check(lib().mdpd_autotune(h, int(reps), C.byref(chosen), _p(ms)), h)
+    return int(chosen.value), ms.tolist()
+
+
 def mdpd_density_noalloc(params, pos_t, rho_t, stream=None):
     """Densities of the particles at device positions pos_t ((n, 3) float64) into
     rho_t ((n,) float64) without any device allocation by the library (fixed
@@ -378,6 +390,9 @@ class System:
 
     def profile(self):
         return mdpd_profile(self.h)
+
+    def autotune(self, reps: int = 5):
+        return mdpd_autotune(self.h, reps)
 
     def describe(self):
         return mdpd_describe(self.h)

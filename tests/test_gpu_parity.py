@@ -277,3 +277,36 @@ def test_list_and_scan_kernels_agree(M):
     assert a.pair_count() == b.pair_count()
     a.close()
     b.close()
+
+
+def test_autotune_keeps_state_and_parity(M):
+    w = I.tiny(4000, (9.0, 9.0, 9.0), 41, ntypes=2)
+    p = w.params.copy(precision=0)
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    s.step(3)
+    x0, v0, _, _ = s.state()
+    chosen, ms = s.autotune(reps=3)
+    assert chosen in (M.KERNELS_NLIST, M.KERNELS_NLIST_THREAD)
+    assert len(ms) == 2 and min(ms) > 0
+    x1, v1, _, _ = s.state()
+    assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
+    o.run(3)
+    f, rho = s.forces()
+    a, _ = o.forces()
+    assert rel_force_err(f, a) <= TOL[0]
+    s.close()
+
+
+def test_sampled_profile_counts(M):
+    w = I.tiny(3000, (8.0, 8.0, 8.0), 42)
+    s = M.System(w.params.copy(precision=1), w.pos, w.vel, w.type, 1)
+    s.set_option(M.OPT_PROFILE, 100)
+    s.set_option(M.OPT_PROFILE_EVERY, 4)
+    s.step(20)
+    prof, steps, launches = s.profile()
+    assert steps == 5
+    _, lps = s.describe()
+    assert launches == 20 * lps + 1
+    assert all(v > 0 for v in prof.values())
+    s.close()
