@@ -350,11 +350,11 @@ void enqueue_bin(mdpd_handle* h, bool gather_a)
 {
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
-    cudaMemsetAsync(h->count, 0, (size_t)h->geo.ncell * sizeof(uint32_t), st);
+    // count[] is zero here: cleared at creation and by every cell sort
     launch_bin_count(st, n, h->cap, h->x[h->cur], h->geo, h->cellof, h->slot, h->count, h->status);
     launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp);
     launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src);
-    launch_cell_sort(st, h->geo.ncell, h->start, h->key, h->src);
+    launch_cell_sort(st, h->geo.ncell, h->start, h->key, h->src, h->count);
     launch_gather(st, h->precision, n, h->cap, h->src, h->cellof, master(h, h->cur),
                   master(h, 1 - h->cur), gather_a, h->geo, h->pos4, h->vel4, h->cell_s);
     h->cur = 1 - h->cur;
@@ -600,6 +600,7 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
     bool ok = cudaMemsetAsync(h->status, 0, sizeof(uint32_t), st) == cudaSuccess &&
               cudaMemsetAsync(h->step, 0, sizeof(uint64_t), st) == cudaSuccess &&
               cudaMemsetAsync(h->red_ticket, 0, sizeof(unsigned), st) == cudaSuccess &&
+              cudaMemsetAsync(h->count, 0, (size_t)h->geo.ncell * sizeof(uint32_t), st) == cudaSuccess &&
               cudaMemsetAsync(h->obs, 0, (2 * MDPD_NUM_OBS + 2) * sizeof(double), st) == cudaSuccess;
     if (ok && n > 0)
         ok = cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), kind, st) == cudaSuccess &&

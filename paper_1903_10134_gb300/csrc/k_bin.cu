@@ -18,6 +18,7 @@ __global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Ge
                             uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
                             uint32_t* __restrict__ count, uint32_t* __restrict__ status)
 {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     int q[3];
@@ -79,6 +80,7 @@ __device__ uint32_t block_exclusive(uint32_t v, uint32_t* total)
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const uint32_t* __restrict__ in,
                                                               int64_t n, uint32_t* __restrict__ sums)
 {
+    pdl_enter();
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t s = 0;
 #pragma unroll
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const uint32_t* __
 // One block: exclusive scan of the nb block sums in place; sums[nb] = total.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(uint32_t* __restrict__ sums, int nb)
 {
+    pdl_enter();
     const int base = threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS], s = 0;
 #pragma unroll
@@ -114,6 +117,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __r
                                                              const uint32_t* __restrict__ sums,
                                                              int nb, uint32_t* __restrict__ out)
 {
+    pdl_enter();
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS], s = 0;
 #pragma unroll
@@ -136,6 +140,7 @@ __global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
                               const uint32_t* __restrict__ id, uint32_t* __restrict__ key,
                               uint32_t* __restrict__ src)
 {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t dst = start[cellof[i]] + slot[i];
@@ -143,12 +148,16 @@ __global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
     src[dst] = (uint32_t)i;
 }
 
-// Insertion sort of each cell's slots by particle id.
+// Insertion sort of each cell's slots by particle id; also clears the cell's
+// count, so the counts are zero whenever a binning starts.
 __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
-                            uint32_t* __restrict__ key, uint32_t* __restrict__ src)
+                            uint32_t* __restrict__ key, uint32_t* __restrict__ src,
+                            uint32_t* __restrict__ count)
 {
+    pdl_enter();
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncell) return;
+    count[c] = 0u;      // the counts are consumed; leave them zero for the next binning
     const uint32_t b = start[c], e = start[c + 1];
     for (uint32_t a = b + 1; a < e; ++a) {
         const uint32_t k = key[a], s = src[a];
@@ -169,6 +178,7 @@ __global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
                          int gather_a, Geo geo, typename Vec4<T>::type* __restrict__ pos4,
                          typename Vec4<T>::type* __restrict__ vel4, uint32_t* __restrict__ cell_s)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t i = src[s];
@@ -204,6 +214,7 @@ __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3
                              const double* __restrict__ vel3, Geo geo, Master m,
                              const uint8_t* __restrict__ type_by_id, uint32_t* __restrict__ status)
 {
+    pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     uint32_t st = 0;
@@ -229,6 +240,7 @@ __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3
 __global__ void k_scatter_vec_by_id(int n, int64_t cap, const uint32_t* __restrict__ id,
                                     const double* __restrict__ v, double* __restrict__ out)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const uint32_t d = id[s];
@@ -240,6 +252,7 @@ template <typename T>
 __global__ void k_scatter_scalar_by_id(int n, const uint32_t* __restrict__ id,
                                        const T* __restrict__ r, double* __restrict__ out)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     out[id[s]] = (double)r[s];
@@ -248,6 +261,7 @@ __global__ void k_scatter_scalar_by_id(int n, const uint32_t* __restrict__ id,
 __global__ void k_scatter_type_by_id(int n, const uint32_t* __restrict__ id,
                                      const uint8_t* __restrict__ t, int32_t* __restrict__ out)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     out[id[s]] = (int32_t)t[s];
@@ -259,7 +273,7 @@ void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, cons
                       uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
 {
     if (n <= 0) return;
-    k_bin_count<<<nblocks(n), BLOCK, 0, st>>>(n, cap, x, geo, cellof, slot, count, status);
+    launch_pdl(k_bin_count, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, x, geo, cellof, slot, count, status);
 }
 
 int scan_num_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
@@ -269,23 +283,23 @@ void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint3
 {
     const int nb = scan_num_blocks(n);
     if (nb <= 0) return;
-    k_scan_blocks<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp);
-    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(tmp, nb);
-    k_scan_apply<<<nb, SCAN_THREADS, 0, st>>>(in, n, tmp, nb, out);
+    launch_pdl(k_scan_blocks, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp);
+    launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), st, tmp, nb);
+    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp, nb, out);
 }
 
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
                         const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src)
 {
     if (n <= 0) return;
-    k_bin_scatter<<<nblocks(n), BLOCK, 0, st>>>(n, cellof, slot, start, id, key, src);
+    launch_pdl(k_bin_scatter, dim3(nblocks(n)), dim3(BLOCK), st, n, cellof, slot, start, id, key, src);
 }
 
 void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
-                      uint32_t* src)
+                      uint32_t* src, uint32_t* count)
 {
     if (ncell <= 0) return;
-    k_cell_sort<<<nblocks(ncell), BLOCK, 0, st>>>(ncell, start, key, src);
+    launch_pdl(k_cell_sort, dim3(nblocks(ncell)), dim3(BLOCK), st, ncell, start, key, src, count);
 }
 
 void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
@@ -294,10 +308,10 @@ void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uin
 {
     if (n <= 0) return;
     if (precision == 0)
-        k_gather<double><<<nblocks(n), BLOCK, 0, st>>>(n, cap, src, cellof, in, out, gather_a,
+        launch_pdl(k_gather<double>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof, in, out, gather_a,
                                                        geo, (D4*)pos4, (D4*)vel4, cell_s);
     else
-        k_gather<float><<<nblocks(n), BLOCK, 0, st>>>(n, cap, src, cellof, in, out, gather_a,
+        launch_pdl(k_gather<float>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof, in, out, gather_a,
                                                       geo, (float4*)pos4, (float4*)vel4, cell_s);
 }
 
@@ -306,14 +320,14 @@ void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
                        const uint8_t* type_by_id, uint32_t* status)
 {
     if (n <= 0) return;
-    k_load_state<<<nblocks(n), BLOCK, 0, st>>>(n, cap, pos3, vel3, geo, m, type_by_id, status);
+    launch_pdl(k_load_state, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, pos3, vel3, geo, m, type_by_id, status);
 }
 
 void launch_scatter_by_id(cudaStream_t st, int n, int64_t cap, const uint32_t* id,
                           const double* vec3, double* out3)
 {
     if (n <= 0) return;
-    k_scatter_vec_by_id<<<nblocks(n), BLOCK, 0, st>>>(n, cap, id, vec3, out3);
+    launch_pdl(k_scatter_vec_by_id, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, id, vec3, out3);
 }
 
 void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const uint32_t* id,
@@ -321,16 +335,16 @@ void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const ui
 {
     if (n <= 0) return;
     if (precision == 0)
-        k_scatter_scalar_by_id<double><<<nblocks(n), BLOCK, 0, st>>>(n, id, (const double*)r, out);
+        launch_pdl(k_scatter_scalar_by_id<double>, dim3(nblocks(n)), dim3(BLOCK), st, n, id, (const double*)r, out);
     else
-        k_scatter_scalar_by_id<float><<<nblocks(n), BLOCK, 0, st>>>(n, id, (const float*)r, out);
+        launch_pdl(k_scatter_scalar_by_id<float>, dim3(nblocks(n)), dim3(BLOCK), st, n, id, (const float*)r, out);
 }
 
 void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const uint8_t* type,
                                int32_t* out)
 {
     if (n <= 0) return;
-    k_scatter_type_by_id<<<nblocks(n), BLOCK, 0, st>>>(n, id, type, out);
+    launch_pdl(k_scatter_type_by_id, dim3(nblocks(n)), dim3(BLOCK), st, n, id, type, out);
 }
 
 }  // namespace mdpd

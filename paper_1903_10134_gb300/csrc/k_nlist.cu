@@ -34,6 +34,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
              const uint32_t* __restrict__ start, T* __restrict__ rho_out,
              uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
@@ -99,6 +100,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
                const uint32_t* __restrict__ start, T* __restrict__ rho_out,
                uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
 {
+    pdl_enter();
     using V = typename Vec4<T>::type;
     __shared__ V hpos[DC_WARPS][DC_GROUP];
     __shared__ uint32_t pre[DC_WARPS][28];
@@ -233,6 +235,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
            const uint64_t* __restrict__ step_ptr, int step_offset, Master m,
            double* __restrict__ out, double* __restrict__ partials, uint32_t* __restrict__ status)
 {
+    pdl_enter();
     using V = typename Vec4<T>::type;
     __shared__ PairTables<T> tab;
     __shared__ T shift[27][3];
@@ -362,7 +365,7 @@ void launch_force_nl_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, cons
     const V* v = (const V*)vel4;
     const T* r = (const T*)rho;
 #define MDPD_FNL(MODE_)                                                                    \
-    k_force_nl<T, MODE_><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, mk, p, v, r, cell_s, \
+    launch_pdl(k_force_nl<T, MODE_>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, mk, p, v, r, cell_s, \
                                                     start, nl, nl_count, step_ptr,        \
                                                     step_offset, m, out, partials, status)
     if (mode == FM_EVAL) MDPD_FNL(FM_EVAL);
@@ -380,10 +383,10 @@ void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const
     if (n <= 0) return;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
     if (precision == 0)
-        k_density_nl<double><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const D4*)pos4, cell_s,
+        launch_pdl(k_density_nl<double>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, (const D4*)pos4, cell_s,
                                                         start, (double*)rho, nl, nl_count);
     else
-        k_density_nl<float><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const float4*)pos4,
+        launch_pdl(k_density_nl<float>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, (const float4*)pos4,
                                                        cell_s, start, (float*)rho, nl, nl_count);
 }
 
@@ -394,10 +397,10 @@ void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t 
     if (ncell <= 0) return;
     const unsigned nb = (unsigned)((ncell + DC_WARPS - 1) / DC_WARPS);
     if (precision == 0)
-        k_density_cell<double><<<nb, DC_WARPS * 32, 0, st>>>(ncell, cap, geo, ph, (const D4*)pos4,
+        launch_pdl(k_density_cell<double>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap, geo, ph, (const D4*)pos4,
                                                              start, (double*)rho, nl, nl_count);
     else
-        k_density_cell<float><<<nb, DC_WARPS * 32, 0, st>>>(ncell, cap, geo, ph,
+        launch_pdl(k_density_cell<float>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap, geo, ph,
                                                             (const float4*)pos4, start,
                                                             (float*)rho, nl, nl_count);
 }

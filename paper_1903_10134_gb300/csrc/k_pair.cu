@@ -18,6 +18,7 @@ k_density(int n, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ po
           const uint32_t* __restrict__ cell_s, const uint32_t* __restrict__ start,
           T* __restrict__ rho_out)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     const T rd2 = (T)(ph.rd * ph.rd);
@@ -81,6 +82,7 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         const uint64_t* __restrict__ step_ptr, int step_offset, Master m,
         double* __restrict__ out, double* __restrict__ partials, uint32_t* __restrict__ status)
 {
+    pdl_enter();
     __shared__ PairTables<T> tab;
     load_tables(tab, ph);
     __syncthreads();
@@ -144,6 +146,7 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
 __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, Master m,
                              uint32_t* __restrict__ status)
 {
+    pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
     if ((ph.frozen >> m.type[s]) & 1u) return;
@@ -181,6 +184,7 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
              double* __restrict__ obs_sum, double* __restrict__ obs_count,
              uint64_t* __restrict__ step_ptr, int advance)
 {
+    pdl_enter();
     __shared__ double sh[NOBS][RED_CHUNK + 1];
     __shared__ double s16[NOBS][17];
     __shared__ bool last;
@@ -253,17 +257,17 @@ void launch_force_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const G
     const T* r = (const T*)rho;
     switch (mode) {
     case FM_EVAL:
-        k_force<T, FM_EVAL><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, mk, p, v, r, cell_s,
+        launch_pdl(k_force<T, FM_EVAL>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, mk, p, v, r, cell_s,
                                                        start, step_ptr, step_offset, m, out,
                                                        partials, status);
         break;
     case FM_LAST:
-        k_force<T, FM_LAST><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, mk, p, v, r, cell_s,
+        launch_pdl(k_force<T, FM_LAST>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, mk, p, v, r, cell_s,
                                                        start, step_ptr, step_offset, m, out,
                                                        partials, status);
         break;
     default:
-        k_force<T, FM_FUSED><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, mk, p, v, r, cell_s,
+        launch_pdl(k_force<T, FM_FUSED>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, mk, p, v, r, cell_s,
                                                         start, step_ptr, step_offset, m, out,
                                                         partials, status);
         break;
@@ -282,10 +286,10 @@ void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const
     if (n <= 0) return;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
     if (precision == 0)
-        k_density<double><<<nb, PAIR_BLOCK, 0, st>>>(n, geo, ph, (const D4*)pos4, cell_s, start,
+        launch_pdl(k_density<double>, dim3(nb), dim3(PAIR_BLOCK), st, n, geo, ph, (const D4*)pos4, cell_s, start,
                                                      (double*)rho);
     else
-        k_density<float><<<nb, PAIR_BLOCK, 0, st>>>(n, geo, ph, (const float4*)pos4, cell_s,
+        launch_pdl(k_density<float>, dim3(nb), dim3(PAIR_BLOCK), st, n, geo, ph, (const float4*)pos4, cell_s,
                                                     start, (float*)rho);
 }
 
@@ -307,7 +311,7 @@ void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, cons
                        const MaskDev& mk, const Master& m, uint32_t* status)
 {
     if (n <= 0) return;
-    k_kick_drift<<<(n + 255) / 256, 256, 0, st>>>(n, cap, geo, ph, mk, m, status);
+    launch_pdl(k_kick_drift, dim3((n + 255) / 256), dim3(256), st, n, cap, geo, ph, mk, m, status);
 }
 
 int reduce_l1_blocks(int nparts) { return (nparts + RED_CHUNK - 1) / RED_CHUNK; }
@@ -317,7 +321,7 @@ void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, doub
                        uint64_t* step_ptr, int advance)
 {
     const int nb = reduce_l1_blocks(nparts) > 0 ? reduce_l1_blocks(nparts) : 1;
-    k_reduce_obs<<<nb, RED_THREADS, 0, st>>>(partials, nparts, l1, ticket, obs, obs_sum,
+    launch_pdl(k_reduce_obs, dim3(nb), dim3(RED_THREADS), st, partials, nparts, l1, ticket, obs, obs_sum,
                                              obs_count, step_ptr, advance);
 }
 

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "mdpd.h"
 
 namespace mdpd {
@@ -64,6 +66,34 @@ enum ForceMode : int {
                     // drift and reflection
 };
 
+// Programmatic dependent launch: every kernel of the time step is launched
+// with programmatic stream serialisation, so it can be scheduled while the
+// previous kernel drains; it waits for the previous grid's completion and
+// memory (griddepcontrol.wait) before touching any data, then lets its own
+// dependent be scheduled (griddepcontrol.launch_dependents).
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 constexpr int OBS_PARTIALS = 16;   // observable slots per partial (14 used)
 
 // ---- launchers (binning / scan) -------------------------------------------
@@ -75,8 +105,9 @@ void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint3
                            uint32_t* tmp);
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
                         const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src);
+// Sorts each cell's slots by key and clears count[] for the next binning.
 void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
-                      uint32_t* src);
+                      uint32_t* src, uint32_t* count);
 void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
                    const uint32_t* cellof, const Master& in, const Master& out, bool gather_a,
                    const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s);

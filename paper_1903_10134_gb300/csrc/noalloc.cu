@@ -218,7 +218,7 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
     k_na_count<<<nb, 256, 0, st>>>(nn, pos, geo, cellof, slot, count);
     launch_exclusive_scan(st, count, geo.ncell, start, scan);
     k_na_scatter<<<nb, 256, 0, st>>>(nn, cellof, slot, start, key, src);
-    launch_cell_sort(st, geo.ncell, start, key, src);
+    launch_cell_sort(st, geo.ncell, start, key, src, count);
     if (p->precision == 0)
         k_na_gather<double><<<nb, 256, 0, st>>>(nn, pos, src, cellof, geo, (D4*)pos4, cells);
     else
