@@ -157,6 +157,25 @@ def _oracle_walls(w) -> dict:
     return {"mask": w.mask, "voxel": w.voxel, "origin": w.origin}
 
 
+def force_traffic(workload: str, precision: str):
+    """DRAM bytes per force-pass launch from the committed ncu summary, or None
+    when there is none for this workload or the kernel sources changed since
+    the counters were taken (the summary records their SHA-1)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"force_traffic_{workload}.json")
+    if precision != "fp32" or not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        h = hashlib.sha1()
+        for src in d["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return d["dram_bytes_per_launch"] if h.hexdigest() == d["source_sha1"] else None
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -322,13 +341,7 @@ def run_ours(args):
         bytes_pp = (36 if prec == 1 else 68) + 96
         hbm_peak = peaks.get("hbm_gbs", 6790.0)
         hbm_ach = n * bytes_pp / (force_ms * 1e-3) / 1e9 if force_ms > 0 else None
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", f"force_traffic_{args.workload}.json")
-        if os.path.exists(tfile):
-            try:
-                traffic = json.load(open(tfile)).get("dram_bytes_per_launch")
-            except (OSError, ValueError):
-                traffic = None
+        traffic = force_traffic(args.workload, args.precision)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
