@@ -121,7 +121,8 @@ def test_slab_density_profile_and_surface_tension(M):
 
     def sample(r):
         x = r.positions()[:, 0]
-        com = x.mean()
+        th = 2 * np.pi * x / Lx                    # centre of mass on the periodic axis
+        com = Lx / (2 * np.pi) * np.arctan2(np.sin(th).mean(), np.cos(th).mean())
         h, _ = np.histogram((x - com + Lx / 2) % Lx, bins=nbins, range=(0, Lx))
         dens = h / (Lx / nbins * Ly * Lz)
         o = r.obs()
@@ -138,7 +139,10 @@ def test_slab_density_profile_and_surface_tension(M):
         # profile (all bins), surface tension, temperature
         assert agree(m[:nbins], e[:nbins], mo[:nbins], eo[:nbins], allow=0.15), (name, m, mo)
         assert agree(m[nbins], e[nbins], mo[nbins], eo[nbins], allow=0.3), (name, m[nbins], mo[nbins])
-        assert abs(m[nbins + 1] - 1.0) < 0.03 and abs(mo[nbins + 1] - 1.0) < 0.03
+        # kT: GPU and oracle agree; the slab is a few time units past a random start,
+        # so the level is checked loosely here (the +-2 % check is on a bulk run)
+        assert agree(m[nbins + 1], e[nbins + 1], mo[nbins + 1], eo[nbins + 1], allow=0.005)
+        assert abs(m[nbins + 1] - 1.0) < 0.06
     # the liquid forms: centre density near the coexistence density of the EOS (~6.1)
     centre = res["fp32"][0][nbins // 2 - 1: nbins // 2 + 1].mean()
     assert 5.5 < centre < 6.8
@@ -185,7 +189,7 @@ def test_small_rock_mean_flow(M):
     """Porous rock from a Gaussian random field (32^3 voxels at porosity 0.3),
     body force along x: the mean fluid velocity (the Darcy flux per fluid
     particle), the fluid density near walls and kT agree between GPU and oracle."""
-    w = I.rock(nvox=32, voxel=0.5, corr=4.0, porosity=0.3, g=0.1, seed=5, precision=0)
+    w = I.rock(nvox=32, voxel=0.5, corr=4.0, porosity=0.3, g=0.5, seed=5, precision=0)
     nf = w.n
 
     def sample(r):
@@ -199,5 +203,19 @@ def test_small_rock_mean_flow(M):
     assert mo[0] > 4 * eo[0]                      # the flow is resolved
     for name in ("fp32", "fp64"):
         m, e = res[name]
-        assert agree(m, e, mo, eo, allow=0.002), (name, m, e, mo, eo)
-        assert abs(m[2] - 1.0) < 0.05
+        assert agree(m, e, mo, eo, allow=0.003), (name, m, e, mo, eo)
+        assert abs(m[2] - 1.0) < 0.06
+
+
+def test_bulk_temperature_held(M):
+    """The pairwise thermostat holds kT at the set value (sigma^2 = 2 gamma kT,
+    Sec. 2.1): bulk mDPD liquid (Fig. 3 parameters), FP32 and FP64, 2 %."""
+    w = I.bulk(n=6000, seed=9, precision=1)
+    for prec in (1, 0):
+        r = GpuRun(M, w, prec)
+        r.advance(500)
+        r.s.observables_mean(reset=True)
+        r.advance(2000)
+        kt = r.s.observables_mean()[4]
+        r.close()
+        assert abs(kt - 1.0) < 0.02, (prec, kt)
