@@ -114,15 +114,37 @@ def bulk(n: int = 6000, L=(10.0, 10.0, 10.0), seed: int = 1, precision: int = 0,
     return Workload("bulk", p, pos, vel, np.zeros(n, np.int32), seed, steps=steps)
 
 
+def lattice_positions(lo, hi, density: float, rng: np.random.Generator,
+                      jitter: float = 0.05) -> np.ndarray:
+    """Simple cubic lattice filling [lo, hi) at about the given number density
+    (an integer number of sites per edge), each site displaced by up to
+    `jitter` lattice spacings."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    a0 = density ** (-1.0 / 3.0)
+    m = np.maximum(1, np.round((hi - lo) / a0)).astype(int)
+    a = (hi - lo) / m
+    g = np.stack(np.meshgrid(*[np.arange(k) for k in m], indexing="ij"), -1).reshape(-1, 3)
+    pos = lo + (g + 0.5) * a
+    return pos + jitter * a * (2 * rng.random(pos.shape) - 1)
+
+
 def slab(box=(60.0, 20.0, 20.0), slab_x=(20.0, 40.0), density: float = 6.0,
-         seed: int = 1, precision: int = 1, steps: int = 20000, **pk) -> Workload:
+         seed: int = 1, precision: int = 1, steps: int = 20000, fill: str = "random",
+         **pk) -> Workload:
     """Liquid-vapour slab (Sec. 4.1 shape): a block of liquid across the full
-    y-z section of a periodic box, vapour elsewhere."""
+    y-z section of a periodic box, vapour elsewhere.  fill = "random" places
+    the particles uniformly at random, "lattice" on a jittered cubic lattice
+    (the paper starts its slab from an fcc lattice)."""
     rng = np.random.default_rng(seed)
     p = MDPDParams(box=tuple(float(x) for x in box), precision=precision, **pk)
-    vol = (slab_x[1] - slab_x[0]) * box[1] * box[2]
-    n = int(round(density * vol))
-    pos = uniform_positions(n, (slab_x[0], 0.0, 0.0), (slab_x[1], box[1], box[2]), rng)
+    lo, hi = (slab_x[0], 0.0, 0.0), (slab_x[1], box[1], box[2])
+    if fill == "lattice":
+        pos = lattice_positions(lo, hi, density, rng)
+    else:
+        vol = (slab_x[1] - slab_x[0]) * box[1] * box[2]
+        pos = uniform_positions(int(round(density * vol)), lo, hi, rng)
+    n = pos.shape[0]
     vel = maxwell_velocities(n, p.kT, rng)
     return Workload("slab", p, pos, vel, np.zeros(n, np.int32), seed, steps=steps)
 

@@ -76,3 +76,41 @@ def test_eos_fits_of_fig3(golden_dir):
     fit = rho + al * A * rho ** 2 + 2 * al * B * rd ** 4 * (rho ** 3 - c * rho ** 2 + d)
     p, e, _ = _dpd_pressure(A, B, rho, 5.0, blocks=5)
     assert abs(p - fit) < 2.5, (p, fit)
+
+
+def _eos_zero(g):
+    """Zero of the Fig. 3b mDPD EOS (alpha reading) near rho = 6, by bisection."""
+    A, B, rd, al, c, d = (g[k] for k in ("mdpd_A", "mdpd_B", "mdpd_rd", "mdpd_alpha",
+                                         "mdpd_c", "mdpd_d"))
+
+    def p(rho):
+        return rho + al * A * rho ** 2 + 2 * al * B * rd ** 4 * (rho ** 3 - c * rho ** 2 + d)
+    lo, hi = 5.0, 8.0
+    assert p(lo) < 0 < p(hi)
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if p(mid) < 0 else (lo, mid)
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.slow
+def test_slab_liquid_density_is_eos_coexistence(golden_dir):
+    """A liquid slab in vacuum (Sec. 4.1 set-up with the Fig. 3b parameters)
+    relaxes to zero pressure, so its interior density is the zero of the
+    printed mDPD equation of state (6.10)."""
+    rho0 = _eos_zero(_golden(golden_dir))
+    assert abs(rho0 - 6.10) < 0.01
+    Lx = 24.0
+    w = I.slab(box=(Lx, 8.0, 8.0), slab_x=(8.0, 16.0), seed=7, precision=0, fill="lattice")
+    o = O.Oracle(w.params, w.pos, w.vel, w.type, w.seed, use_cells=True)
+    o.run(600)
+    prof = []
+    for _ in range(12):
+        o.run(50)
+        x = o.x[:, 0]
+        th = 2 * np.pi * x / Lx
+        com = Lx / (2 * np.pi) * np.arctan2(np.sin(th).mean(), np.cos(th).mean())
+        h, _ = np.histogram((x - com + Lx / 2) % Lx, bins=12, range=(0, Lx))
+        prof.append(h / (2.0 * 64.0))
+    centre = np.mean(prof, axis=0)[4:8].mean()
+    assert abs(centre - rho0) < 0.15, centre
