@@ -26,7 +26,10 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 
 // Thread-per-particle variant: each thread scans its 27 neighbour cells and
 // stores its partners straight to the slot-major list (no shared-memory
-// staging, so occupancy is set by registers alone).
+// staging, so occupancy is set by registers alone).  The candidate loop is
+// branch-free: the density weight is evaluated for every candidate and
+// clamped at zero beyond r_d, the list store is predicated, and the thread's
+// own (r = 0) density term is subtracted once at the end.
 template <typename T>
 __global__ void __launch_bounds__(PAIR_BLOCK, 12)
 k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
@@ -37,15 +40,16 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
+    const T rc2 = (T)(ph.rc * ph.rc);
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const auto pi = pos4[s];
     const bool mobile = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
-    T acc = ph.rho_self ? cw : T(0);
+    T acc = T(0);
     uint32_t cnt = 0;
+    uint32_t* my = nl + s;
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
         if (z < 0) continue;
@@ -61,24 +65,22 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
                 const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
                 const uint32_t b = start[nc], e = start[nc + 1];
+#pragma unroll 2
                 for (uint32_t j = b; j < e; ++j) {
                     const auto pj = pos4[j];
                     const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    const bool other = j != (uint32_t)s;
-                    if (other && r2 < rd2) {
-                        const T w = T(1) - sqrt_t(r2) * inv_rd;
-                        acc += cw * w * w;
-                    }
-                    if (other && mobile && r2 < rc2 && r2 > T(0)) {
-                        if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
-                        ++cnt;
-                    }
+                    const T wr = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
+                    acc += cw * wr * wr;
+                    const bool hit = mobile && r2 < rc2 && r2 > T(0);
+                    if (hit && cnt < NL_MAX) my[(int64_t)cnt * cap] = (j << 5) | code;
+                    cnt += hit ? 1u : 0u;
                 }
             }
         }
     }
-    rho_out[s] = acc;
+    // the loop counted the thread itself once, at r = 0 (weight cw)
+    rho_out[s] = acc - (ph.rho_self ? T(0) : cw);
     nl_count[s] = cnt;
 }
 
@@ -139,7 +141,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
     if (lane == 27) pre[w][27] = C;
     __syncwarp();
 
-    const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
+    const T rc2 = (T)(ph.rc * ph.rc);
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const T hx = (T)geo.h[0], hy = (T)geo.h[1], hz = (T)geo.h[2];
@@ -179,13 +181,12 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
                     const T dy = pi.y - shy - pj.y;
                     const T dz = pi.z - shz - pj.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    const bool other = valid && j != g0 + (uint32_t)i;
-                    if (other && r2 < rd2) {
-                        const T wr = T(1) - sqrt_t(r2) * inv_rd;
-                        acc[i] += cw * wr * wr;
-                    }
+                    // branch-free weight; the home particle's own r = 0 term is
+                    // removed after the loop
+                    const T wr = valid ? max(T(1) - sqrt0_t(r2) * inv_rd, T(0)) : T(0);
+                    acc[i] += cw * wr * wr;
                     const bool mob = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
-                    const bool hc = other && mob && r2 < rc2 && r2 > T(0);
+                    const bool hc = valid && mob && r2 < rc2 && r2 > T(0);
                     const unsigned m = __ballot_sync(0xffffffffu, hc);
                     if (m) {
                         const uint32_t slot = cnt[i] + (uint32_t)__popc(m & lt);
@@ -203,7 +204,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
                 if (lane == 0) {
-                    rho_out[g0 + i] = (ph.rho_self ? cw : T(0)) + v;
+                    rho_out[g0 + i] = v - (ph.rho_self ? T(0) : cw);
                     nl_count[g0 + i] = cnt[i];
                 }
                 const uint32_t kept = cnt[i] < (uint32_t)NL_MAX ? cnt[i] : (uint32_t)NL_MAX;

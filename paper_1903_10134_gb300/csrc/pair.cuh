@@ -20,6 +20,9 @@ __device__ __forceinline__ double rsqrt_t(double x) { return 1.0 / sqrt(x); }
 // square root (about 2 ulp), FP64 correctly rounded.
 __device__ __forceinline__ float sqrt_t(float x) { return x * rsqrtf(x); }
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+// Same for r^2 >= 0, giving 0 at 0.
+__device__ __forceinline__ float sqrt0_t(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
+__device__ __forceinline__ double sqrt0_t(double x) { return sqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T xi_of(U4 w, int dist)
