@@ -26,10 +26,10 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 
 // Thread-per-particle variant: each thread scans its 27 neighbour cells and
 // stores its partners straight to the slot-major list (no shared-memory
-// staging, so occupancy is set by registers alone).  The candidate loop is
-// branch-free: the density weight is evaluated for every candidate and
-// clamped at zero beyond r_d, the list store is predicated, and the thread's
-// own (r = 0) density term is subtracted once at the end.
+// staging, so occupancy is set by registers alone).  The density term is
+// evaluated under a branch: on the large porous systems this variant is picked
+// for, most warps have no candidate within r_d in an iteration, and a
+// branch-free weight (a reciprocal square root per candidate) measured slower.
 template <typename T>
 __global__ void __launch_bounds__(PAIR_BLOCK, 12)
 k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
@@ -40,16 +40,15 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const T rc2 = (T)(ph.rc * ph.rc);
+    const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const auto pi = pos4[s];
     const bool mobile = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
-    T acc = T(0);
+    T acc = ph.rho_self ? cw : T(0);
     uint32_t cnt = 0;
-    uint32_t* my = nl + s;
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
         if (z < 0) continue;
@@ -65,22 +64,24 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
                 const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
                 const uint32_t b = start[nc], e = start[nc + 1];
-#pragma unroll 2
                 for (uint32_t j = b; j < e; ++j) {
                     const auto pj = pos4[j];
                     const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    const T wr = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
-                    acc += cw * wr * wr;
-                    const bool hit = mobile && r2 < rc2 && r2 > T(0);
-                    if (hit && cnt < NL_MAX) my[(int64_t)cnt * cap] = (j << 5) | code;
-                    cnt += hit ? 1u : 0u;
+                    const bool other = j != (uint32_t)s;
+                    if (other && r2 < rd2) {
+                        const T w = T(1) - sqrt_t(r2) * inv_rd;
+                        acc += cw * w * w;
+                    }
+                    if (other && mobile && r2 < rc2 && r2 > T(0)) {
+                        if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
+                        ++cnt;
+                    }
                 }
             }
         }
     }
-    // the loop counted the thread itself once, at r = 0 (weight cw)
-    rho_out[s] = acc - (ph.rho_self ? T(0) : cw);
+    rho_out[s] = acc;
     nl_count[s] = cnt;
 }
 
@@ -226,6 +227,8 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
 // on the leading lanes (frozen wall particles need no force), then each of
 // those lanes walks its list with a two-stage software prefetch: list entries
 // two ahead, partner data one ahead.
+constexpr int NKEY = NL_MAX + 2;   // list lengths 0..NL_MAX, and "more" (direct scan)
+
 template <typename T, int MODE>
 __global__ void __launch_bounds__(PAIR_BLOCK)
 k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
@@ -241,7 +244,8 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     __shared__ PairTables<T> tab;
     __shared__ T shift[27][3];
     __shared__ int act[PAIR_BLOCK];
-    __shared__ int wsum[PAIR_BLOCK / 32];
+    __shared__ int hist[PAIR_BLOCK / 32][NKEY];
+    __shared__ int kbase[NKEY + 1];
     load_tables(tab, ph);
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
@@ -249,20 +253,53 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
         shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
     }
-    // compact the block's mobile particles onto the first lanes, in cell order
+    for (int k = threadIdx.x; k < (PAIR_BLOCK / 32) * NKEY; k += PAIR_BLOCK) (&hist[0][0])[k] = 0;
+    // Assign the block's mobile particles to lanes in order of decreasing list
+    // length (ties in cell order), so the lanes of a warp walk lists of similar
+    // length; frozen wall particles need no force and get no lane.  A stable
+    // counting sort: per-warp histograms of the length classes, a prefix over
+    // the classes from the longest down, and the rank among equal classes from
+    // the earlier warps and the earlier lanes.
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
     const bool mob0 = s0 < n && ((ph.frozen >> m.type[s0]) & 1u) == 0u;
-    const unsigned bal = __ballot_sync(0xffffffffu, mob0);
-    if (lane == 0) wsum[warp] = __popc(bal);
-    __syncthreads();
-    int woff = 0, nact = 0;
-#pragma unroll
-    for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
-        woff += w < warp ? wsum[w] : 0;
-        nact += wsum[w];
+    int key = -1;
+    if (mob0) {
+        const uint32_t c0 = nl_count[s0];
+        key = c0 > (uint32_t)NL_MAX ? NL_MAX + 1 : (int)c0;
     }
-    if (mob0) act[woff + __popc(bal & ((1u << lane) - 1u))] = s0;
+    __syncthreads();
+    if (key >= 0) atomicAdd(&hist[warp][key], 1);
+    __syncthreads();
+    if (warp == 0) {
+        // kbase[k] = number of particles in classes above k (descending order)
+        int carry = 0;
+        for (int d0 = 0; d0 < NKEY; d0 += 32) {
+            const int d = d0 + lane;
+            const int k = NKEY - 1 - d;
+            int t = 0;
+            if (d < NKEY)
+#pragma unroll
+                for (int w = 0; w < PAIR_BLOCK / 32; ++w) t += hist[w][k];
+            int inc = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += u;
+            }
+            if (d < NKEY) kbase[k] = carry + inc - t;
+            carry += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (lane == 0) kbase[NKEY] = carry;
+    }
+    __syncthreads();
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key >= 0) {
+        int r = kbase[key] + __popc(peers & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) r += hist[w][key];
+        act[r] = s0;
+    }
+    const int nact = kbase[NKEY];
     if (MODE == FM_EVAL && s0 < n && !mob0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k * cap + s0] = 0.0;
