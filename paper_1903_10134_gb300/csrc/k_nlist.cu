@@ -227,8 +227,6 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
 // on the leading lanes (frozen wall particles need no force), then each of
 // those lanes walks its list with a two-stage software prefetch: list entries
 // two ahead, partner data one ahead.
-constexpr int NKEY = NL_MAX + 2;   // list lengths 0..NL_MAX, and "more" (direct scan)
-
 template <typename T, int MODE>
 __global__ void __launch_bounds__(PAIR_BLOCK)
 k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
@@ -244,8 +242,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     __shared__ PairTables<T> tab;
     __shared__ T shift[27][3];
     __shared__ int act[PAIR_BLOCK];
-    __shared__ int hist[PAIR_BLOCK / 32][NKEY];
-    __shared__ int kbase[NKEY + 1];
+    __shared__ int wsum[PAIR_BLOCK / 32];
     load_tables(tab, ph);
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
@@ -253,53 +250,20 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
         shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
     }
-    for (int k = threadIdx.x; k < (PAIR_BLOCK / 32) * NKEY; k += PAIR_BLOCK) (&hist[0][0])[k] = 0;
-    // Assign the block's mobile particles to lanes in order of decreasing list
-    // length (ties in cell order), so the lanes of a warp walk lists of similar
-    // length; frozen wall particles need no force and get no lane.  A stable
-    // counting sort: per-warp histograms of the length classes, a prefix over
-    // the classes from the longest down, and the rank among equal classes from
-    // the earlier warps and the earlier lanes.
+    // compact the block's mobile particles onto the first lanes, in cell order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
     const bool mob0 = s0 < n && ((ph.frozen >> m.type[s0]) & 1u) == 0u;
-    int key = -1;
-    if (mob0) {
-        const uint32_t c0 = nl_count[s0];
-        key = c0 > (uint32_t)NL_MAX ? NL_MAX + 1 : (int)c0;
-    }
+    const unsigned bal = __ballot_sync(0xffffffffu, mob0);
+    if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
-    if (key >= 0) atomicAdd(&hist[warp][key], 1);
-    __syncthreads();
-    if (warp == 0) {
-        // kbase[k] = number of particles in classes above k (descending order)
-        int carry = 0;
-        for (int d0 = 0; d0 < NKEY; d0 += 32) {
-            const int d = d0 + lane;
-            const int k = NKEY - 1 - d;
-            int t = 0;
-            if (d < NKEY)
+    int woff = 0, nact = 0;
 #pragma unroll
-                for (int w = 0; w < PAIR_BLOCK / 32; ++w) t += hist[w][k];
-            int inc = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += u;
-            }
-            if (d < NKEY) kbase[k] = carry + inc - t;
-            carry += __shfl_sync(0xffffffffu, inc, 31);
-        }
-        if (lane == 0) kbase[NKEY] = carry;
+    for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
+        woff += w < warp ? wsum[w] : 0;
+        nact += wsum[w];
     }
-    __syncthreads();
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (key >= 0) {
-        int r = kbase[key] + __popc(peers & ((1u << lane) - 1u));
-        for (int w = 0; w < warp; ++w) r += hist[w][key];
-        act[r] = s0;
-    }
-    const int nact = kbase[NKEY];
+    if (mob0) act[woff + __popc(bal & ((1u << lane) - 1u))] = s0;
     if (MODE == FM_EVAL && s0 < n && !mob0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k * cap + s0] = 0.0;
