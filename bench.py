@@ -224,6 +224,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate_ranks(ms: float, n: int, steps: int, world: int, device=None):
+    """Whole-job throughput of independent replicas, one per rank: the slowest
+    rank's timed milliseconds (MAX all-reduce) and all ranks' particle-steps
+    divided by it.  Works with any torch.distributed backend (nccl on GPUs,
+    gloo on CPU)."""
+    import torch
+    t = torch.tensor([ms, float(n)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        m = t[:1].clone()
+        dist.all_reduce(m, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms_max, n_all = float(m.item()), float(tot.item())
+    else:
+        ms_max, n_all = float(ms), float(n)
+    return ms_max, n_all * steps / (ms_max * 1e-3)
+
+
+def replica_seed(rank: int) -> int:
+    """Seed of the replica advanced by a rank (independent replicas)."""
+    return 1 + rank
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -239,7 +263,7 @@ def run_ours(args):
 
     dev = torch.cuda.current_device()
     prec = 0 if args.precision == "fp64" else 1
-    w = make_workload(args.workload, prec, seed=1 + rank, nvox=args.nvox)
+    w = make_workload(args.workload, prec, seed=replica_seed(rank), nvox=args.nvox)
     stream = torch.cuda.Stream()
     s = mdpd.System.from_workload(w, stream=stream)
     tuned = None
@@ -297,11 +321,7 @@ def run_ours(args):
     s.sync()
     prof, prof_steps, launches = s.profile()
 
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * n * K / (ms_max * 1e-3)
+    ms_max, value = aggregate_ranks(ms, n, K, world, device=dev)
 
     # end-to-end through the host-pointer C ABI: per step upload x, v from
     # pinned host memory, one step, read x, v back into pinned host memory
