@@ -578,3 +578,107 @@ int orc_forces_subset(const orc_sys *s, int64_t n, const double *x, const double
     if (s->use_cells) cells_free(&c);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Vector-Jacobian product of one force evaluation.                          */
+/* The force evaluation maps (x, u, theta) to a_i = sum_j f_ij for mobile i   */
+/* (Sec. 2.1, Eq. 1), with rho_i = sum_j w_rho(r_ij) recomputed from x and u  */
+/* the velocities the dissipative term sees.  Given abar (3n), it returns     */
+/* xbar = (da/dx)^T abar, ubar = (da/du)^T abar and tbar[3][8][8], the        */
+/* gradient of L = sum_i abar_i . a_i with respect to the symmetric           */
+/* parameters A, B, gamma (entry [a][b] = [b][a] = dL/dP_ab).  The random     */
+/* draws xi_ij of the given step are held fixed.  Written from the chain rule */
+/* on each ordered pair (i mobile, j): with d = x_i - x_j, r = |d|, e = d/r,  */
+/* w = e.u_ij and f_ij = s e,                                                  */
+/*   s = A wc + B (rho_i + rho_j) wd [r < r_d] - gamma wc^2 w                  */
+/*       + sigma wc xi / sqrt(dt),                                             */
+/*   d(abar_i.f_ij)/dd = (abar_i.e)(s_r e + s_w (u_ij - w e)/r)               */
+/*                       + s (abar_i - (abar_i.e) e)/r,                        */
+/* s_r the r-derivative of s at fixed w and rho, s_w = -gamma wc^2; then the   */
+/* density chain rho_bar_k = dL/drho_k sent back through w_rho'(r) e.          */
+/* ------------------------------------------------------------------------ */
+int orc_force_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
+                  const int32_t *type, const uint32_t *id, uint64_t step,
+                  const double *abar, double *xbar, double *ubar, double *tbar)
+{
+    double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    double *rbar = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+    if (!rho || !rbar) { free(rho); free(rbar); return -2; }
+    if (orc_density(s, n, x, rho) != 0) { free(rho); free(rbar); return -1; }
+    for (int64_t k = 0; k < 3 * n; ++k) { xbar[k] = 0.0; ubar[k] = 0.0; }
+    for (int k = 0; k < 3 * ORC_MAXT * ORC_MAXT; ++k) tbar[k] = 0.0;
+    const double rc = s->rc, rd = s->rd;
+    const double sq_dt = sqrt(s->dt);
+    const double pi = 3.14159265358979323846264338327950288;
+    const double cw = 15.0 / (2.0 * pi * rd * rd * rd);
+    /* force part (serial, plain) */
+    for (int64_t i = 0; i < n; ++i) {
+        if (is_frozen(s, type[i])) continue;
+        const double *ab = &abar[3 * i];
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            pair_vec(s, &x[3 * i], &x[3 * j], d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rc * rc) || !(r2 > 0.0)) continue;
+            const int32_t ti = type[i], tj = type[j];
+            double r = sqrt(r2), e[3], uij[3];
+            for (int k = 0; k < 3; ++k) { e[k] = d[k] / r; uij[k] = u[3 * i + k] - u[3 * j + k]; }
+            double w = e[0] * uij[0] + e[1] * uij[1] + e[2] * uij[2];
+            double wc = 1.0 - r / rc;
+            double A = s->A[ti][tj], B = s->B[ti][tj], g = s->gamma[ti][tj];
+            double sig = sqrt(2.0 * g * s->kT);
+            double xi = orc_xi(s->seed, step, id[i], id[j], s->xi_dist);
+            int near = r < rd;
+            double wd = near ? 1.0 - r / rd : 0.0;
+            double sval = A * wc + B * (rho[i] + rho[j]) * wd - g * wc * wc * w + sig * wc * xi / sq_dt;
+            double s_r = -A / rc - (near ? B * (rho[i] + rho[j]) / rd : 0.0)
+                         + 2.0 * g * wc * w / rc - sig * xi / (sq_dt * rc);
+            double s_w = -g * wc * wc;
+            double ae = ab[0] * e[0] + ab[1] * e[1] + ab[2] * e[2];
+            for (int k = 0; k < 3; ++k) {
+                double gd = ae * (s_r * e[k] + s_w * (uij[k] - w * e[k]) / r)
+                            + sval * (ab[k] - ae * e[k]) / r;
+                xbar[3 * i + k] += gd;
+                xbar[3 * j + k] -= gd;
+                double gu = ae * s_w * e[k];
+                ubar[3 * i + k] += gu;
+                ubar[3 * j + k] -= gu;
+            }
+            if (near) {
+                rbar[i] += ae * B * wd;
+                rbar[j] += ae * B * wd;
+            }
+            int a = ti < tj ? ti : tj, b = ti < tj ? tj : ti;
+            double dsig = g > 0.0 ? s->kT / sig : 0.0;
+            double gA = ae * wc, gB = ae * (rho[i] + rho[j]) * wd;
+            double gG = ae * (-wc * wc * w + dsig * wc * xi / sq_dt);
+            tbar[0 * 64 + a * 8 + b] += gA;
+            tbar[1 * 64 + a * 8 + b] += gB;
+            tbar[2 * 64 + a * 8 + b] += gG;
+        }
+    }
+    /* density part: rho_k = sum_m w_rho(r_km) */
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d[3];
+            pair_vec(s, &x[3 * i], &x[3 * j], d);
+            double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            if (!(r2 < rd * rd) || !(r2 > 0.0)) continue;
+            double r = sqrt(r2);
+            double dw = -2.0 * cw * (1.0 - r / rd) / rd;      /* w_rho'(r) */
+            for (int k = 0; k < 3; ++k) {
+                double gk = rbar[i] * dw * d[k] / r;          /* d rho_i / d x_i */
+                xbar[3 * i + k] += gk;
+                xbar[3 * j + k] -= gk;
+            }
+        }
+    }
+    for (int q = 0; q < 3; ++q)
+        for (int a = 0; a < 8; ++a)
+            for (int b = a + 1; b < 8; ++b) tbar[q * 64 + b * 8 + a] = tbar[q * 64 + a * 8 + b];
+    free(rho);
+    free(rbar);
+    return 0;
+}

@@ -68,6 +68,7 @@ def lib():
         _lib.orc_place_walls.restype = i64
         _lib.orc_num_threads.restype = C.c_int
         _lib.orc_forces_subset.argtypes = [P, i64, P, P, P, P, P, u64, i64, P, P]
+        _lib.orc_force_vjp.argtypes = [P, i64, P, P, P, P, u64, P, P, P, P]
     return _lib
 
 
@@ -226,6 +227,22 @@ class Oracle:
                                    idx.shape[0], _ptr(idx), _ptr(a)) != 0:
             raise RuntimeError("oracle forces failed")
         return a
+
+    def force_vjp(self, abar, x=None, u=None, step=None):
+        """(xbar, ubar, tbar) of L = sum_i abar_i . a_i(x, u, theta) at a fixed
+        random stream; tbar[q][a][b] for q = A, B, gamma (symmetric entries)."""
+        x = self.x if x is None else _c(x, np.float64)
+        u = self.v if u is None else _c(u, np.float64)
+        step = self.step if step is None else step
+        ab = _c(abar, np.float64)
+        xb = np.zeros_like(x)
+        ub = np.zeros_like(x)
+        tb = np.zeros((3, MAXT, MAXT))
+        if lib().orc_force_vjp(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(u), _ptr(self.type),
+                               _ptr(self.ids), int(step), _ptr(ab), _ptr(xb), _ptr(ub),
+                               _ptr(tb)) != 0:
+            raise RuntimeError("oracle vjp failed")
+        return xb, ub, tb
 
     def refresh(self):
         """Recompute rho and a(t) of the current state (step index unchanged)."""
