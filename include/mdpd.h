@@ -200,6 +200,37 @@ enum { MDPD_K_BIN = 0, MDPD_K_DENSITY = 1, MDPD_K_FORCE = 2, MDPD_K_OTHER = 3,
 int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps,
                  int64_t* launches);
 
+/* Replace the parameters of a handle between steps.  Only A, B, gamma, kT, dt,
+ * g, frozen_type_mask, xi_dist and rho_self may differ; box, periodicity, rc,
+ * rd, ntypes and precision must match the handle's.  The next step (or
+ * mdpd_forces / mdpd_set_state) uses the new values.  Synchronises. */
+int mdpd_set_params(mdpd_handle* h, const mdpd_params* params);
+
+/* Set the step index: the next force evaluation of mdpd_step uses step + 1,
+ * mdpd_forces / mdpd_set_state / mdpd_force_vjp_dev use step (this selects the
+ * Philox draws).  Synchronises. */
+int mdpd_set_step(mdpd_handle* h, int64_t step);
+
+/* Device copy (id order, 3N doubles) of the acceleration the next half-kick
+ * will use: a(t) of the current state.  Synchronises. */
+int mdpd_get_accel_dev(mdpd_handle* h, double* accel);
+
+/* Vector-Jacobian product of one force evaluation (the adjoint of Sec. 2.1 /
+ * Eq. 1 at a fixed random stream), at the current positions, the current
+ * velocities (those the dissipative term sees) and the current step index.
+ * abar: device, 3N doubles (id order), the adjoint of the accelerations
+ * a_i = sum_j F_ij + g of mobile particles (rows of frozen particles are
+ * ignored).  Outputs (device, may be NULL): xbar, ubar 3N doubles (id order):
+ * d(sum_i abar_i . a_i)/dx and /du, the position part including the path
+ * through the local densities rho_i; theta_bar 3*8*8 doubles: the gradient with
+ * respect to the symmetric tables A, B, gamma ([q][a][b] = [q][b][a] = dL/dP_ab;
+ * the gamma entry includes sigma = sqrt(2 gamma kT)).  Parameter gradients are
+ * summed with floating-point atomics (last-bit differences between runs).
+ * Errors: TILE_OVERFLOW if a particle has more than 64 partners within r_c.
+ * Synchronises. */
+int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
+                       double* theta_bar);
+
 /* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD)
  * on the current state, reps launches each, and keep the faster one.  The
  * trajectory is not advanced.  chosen (may be NULL) receives the variant, ms

@@ -1006,6 +1006,89 @@ int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps, int
     return MDPD_OK;
 }
 
+int mdpd_set_params(mdpd_handle* h, const mdpd_params* p)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    std::string why;
+    int rc = validate_params(p, why);
+    if (rc) return h->fail(rc, why);
+    for (int k = 0; k < 3; ++k)
+        if (p->box[k] != h->p.box[k] || p->box_lo[k] != h->p.box_lo[k] ||
+            p->periodic[k] != h->p.periodic[k])
+            return h->fail(MDPD_ERR_INVALID_ARG, "the box cannot change");
+    if (p->rc != h->p.rc || p->rd != h->p.rd || p->precision != h->p.precision ||
+        p->ntypes != h->p.ntypes)
+        return h->fail(MDPD_ERR_INVALID_ARG, "rc, rd, precision and ntypes cannot change");
+    if ((rc = sync_check(h))) return rc;
+    h->p = *p;
+    setup_geo_phys(h);
+    destroy_graphs(h);
+    return MDPD_OK;
+}
+
+int mdpd_set_step(mdpd_handle* h, int64_t step)
+{
+    if (!h || step < 0) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    const uint64_t s = (uint64_t)step;
+    CK(cudaMemcpy(h->step, &s, sizeof(s), cudaMemcpyHostToDevice));
+    h->steps_host = step;
+    return MDPD_OK;
+}
+
+int mdpd_get_accel_dev(mdpd_handle* h, double* accel)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    if ((rc = check_ptr_kind(h, accel, true))) return rc;
+    if (accel) launch_scatter_by_id(h->stream, (int)h->n, h->cap, h->id[h->cur], h->a[h->cur], accel);
+    CK(cudaGetLastError());
+    return sync_check(h);
+}
+
+int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
+                       double* theta_bar)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    if (!abar) return h->fail(MDPD_ERR_INVALID_ARG, "abar is required");
+    if ((rc = check_ptr_kind(h, abar, true)) || (rc = check_ptr_kind(h, xbar, true)) ||
+        (rc = check_ptr_kind(h, ubar, true)) || (rc = check_ptr_kind(h, theta_bar, true)))
+        return rc;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    h->ph.list_all = 1;                      // partners of frozen particles too
+    rc = evaluate(h, h->fout, true);
+    h->ph.list_all = 0;
+    if (rc) return rc;
+    const int c = h->cur;
+    double* xs = h->x[1 - c];                // scratch: [3][cap] each, rbar [cap]
+    double* us = h->v[1 - c];
+    double* rs = h->a[1 - c];
+    double* tb = theta_bar ? theta_bar : h->fout;
+    CK(cudaMemsetAsync(tb, 0, 3 * 64 * sizeof(double), st));
+    launch_force_vjp(st, h->precision, n, h->cap, h->geo, h->ph, h->pos4, h->vel4, h->rho, h->nl,
+                     h->nl_count, h->step, abar, xs, us, rs, tb, h->status);
+    if (xbar) launch_scatter_by_id(st, n, h->cap, h->id[c], xs, xbar);
+    if (ubar) launch_scatter_by_id(st, n, h->cap, h->id[c], us, ubar);
+    CK(cudaGetLastError());
+    rc = sync_check(h);
+    if (rc) return rc;
+    if (theta_bar) {
+        // symmetric parameters: mirror the a <= b entries
+        double t[3 * 64];
+        CK(cudaMemcpy(t, theta_bar, sizeof(t), cudaMemcpyDeviceToHost));
+        for (int q = 0; q < 3; ++q)
+            for (int a = 0; a < 8; ++a)
+                for (int b = a + 1; b < 8; ++b) t[q * 64 + b * 8 + a] = t[q * 64 + a * 8 + b];
+        CK(cudaMemcpy(theta_bar, t, sizeof(t), cudaMemcpyHostToDevice));
+    }
+    return MDPD_OK;
+}
+
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;

@@ -44,7 +44,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const auto pi = pos4[s];
-    const bool mobile = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+    const bool mobile = ph.list_all || ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
     T acc = ph.rho_self ? cw : T(0);
@@ -186,7 +186,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
                     // removed after the loop
                     const T wr = valid ? max(T(1) - sqrt0_t(r2) * inv_rd, T(0)) : T(0);
                     acc[i] += cw * wr * wr;
-                    const bool mob = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+                    const bool mob = ph.list_all || ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
                     const bool hc = valid && mob && r2 < rc2 && r2 > T(0);
                     const unsigned m = __ballot_sync(0xffffffffu, hc);
                     if (m) {

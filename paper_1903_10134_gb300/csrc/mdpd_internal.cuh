@@ -34,6 +34,7 @@ struct Phys {
     int ntypes;
     int xi_dist;
     int rho_self;
+    int list_all;                 // 1: the density pass lists partners of frozen particles too
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
     double A[64], B[64], gamma[64], sigma[64];
 };
@@ -148,6 +149,16 @@ int reduce_l1_blocks(int nparts);
 void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
                        unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
                        uint64_t* step_ptr, int advance);
+
+// ---- launchers (adjoint) ---------------------------------------------------
+// VJP of one force evaluation at the current cell-ordered state (lists built
+// with list_all); xbar, ubar component-major [3][cap], rbar [cap] scratch,
+// tbar [3][64] accumulated with atomics (zero it first).
+void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                      const Phys& ph, const void* pos4, const void* vel4, const void* rho,
+                      const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,
+                      const double* abar, double* xbar, double* ubar, double* rbar, double* tbar,
+                      uint32_t* status);
 
 // ---- launchers (walls) -----------------------------------------------------
 void launch_mask_pack(cudaStream_t st, const uint8_t* mask, int64_t nvox, uint32_t* bits);

@@ -92,7 +92,8 @@ SYMBOLS = (
     "mdpd_set_state", "mdpd_set_state_dev", "mdpd_forces", "mdpd_forces_dev",
     "mdpd_observables", "mdpd_observables_mean", "mdpd_pair_count", "mdpd_set_option",
     "mdpd_profile",
-    "mdpd_describe", "mdpd_autotune", "mdpd_density_noalloc", "mdpd_destroy",
+    "mdpd_describe", "mdpd_autotune", "mdpd_set_params", "mdpd_set_step",
+    "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error",
 )
 
@@ -132,6 +133,10 @@ def lib(build_if_stale: bool = True):
     L.mdpd_describe.argtypes = [P, P, C.POINTER(i32)]
     L.mdpd_density_noalloc.argtypes = [P, i64, P, P, P]
     L.mdpd_autotune.argtypes = [P, i32, C.POINTER(i32), P]
+    L.mdpd_set_params.argtypes = [P, P]
+    L.mdpd_set_step.argtypes = [P, i64]
+    L.mdpd_get_accel_dev.argtypes = [P, P]
+    L.mdpd_force_vjp_dev.argtypes = [P, P, P, P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -310,6 +315,26 @@ def mdpd_describe(h):
     return nc.tolist(), int(lps.value)
 
 
+def mdpd_set_params(h, params):
+    cp = to_c_params(params)
+    _check(lib().mdpd_set_params(h, C.byref(cp)), h)
+
+
+def mdpd_set_step(h, step: int):
+    _check(lib().mdpd_set_step(h, int(step)), h)
+
+
+def mdpd_get_accel_dev(h, accel_t):
+    _check(lib().mdpd_get_accel_dev(h, _tptr(accel_t)), h)
+
+
+def mdpd_force_vjp_dev(h, abar_t, xbar_t=None, ubar_t=None, theta_bar_t=None):
+    """VJP of one force evaluation at the current state (device tensors:
+    abar/xbar/ubar (n, 3) float64, theta_bar (3, 8, 8) float64)."""
+    _check(lib().mdpd_force_vjp_dev(h, _tptr(abar_t), _tptr(xbar_t), _tptr(ubar_t),
+                                    _tptr(theta_bar_t)), h)
+
+
 def mdpd_autotune(h, reps: int = 5):
     """Pick the faster density-pass variant on the current state; returns
     (chosen variant, [ms of each variant])."""
@@ -356,6 +381,7 @@ class System:
 
     def set_walls(self, *a, **k):
         mdpd_set_walls(self.h, *a, **k)
+        self.has_walls = True
 
     def step(self, nsteps: int):
         mdpd_step(self.h, nsteps)

@@ -1,0 +1,114 @@
+"""Adjoint of the force evaluation and of velocity-Verlet windows on the GPU,
+against the oracle's adjoint (itself pinned by finite differences) and against
+central finite differences of the GPU forward."""
+import numpy as np
+import pytest
+
+from oracle import adjoint as OAD
+from oracle import oracle as O
+from paper_1903_10134_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1903_10134_gb300 import adjoint as AD, mdpd
+    mdpd.lib()
+    return torch, mdpd, AD
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (1, 2e-4)])
+@pytest.mark.parametrize("frozen", [(), (1,)])
+def test_force_vjp_matches_oracle(env, precision, tol, frozen):
+    torch, M, AD = env
+    w = I.tiny(1500, (6.0, 6.5, 5.5), 12, ntypes=2, frozen_types=frozen, g=(0.1, 0, 0))
+    p = w.params.copy(precision=precision)
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    M.mdpd_set_step(s.h, 7)
+    s.set_state(w.pos, w.vel)
+    abar = np.random.default_rng(3).normal(size=w.pos.shape)
+    xb, ub, tb = AD.force_vjp(s, torch.tensor(abar, device="cuda"))
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed, use_cells=True)
+    oxb, oub, otb = o.force_vjp(abar, step=7)
+    assert _rel(xb.cpu().numpy(), oxb) < tol
+    assert _rel(ub.cpu().numpy(), oub) < tol
+    for q in range(3):
+        assert _rel(tb[q, :2, :2].cpu().numpy(), otb[q, :2, :2]) < tol * 10, q
+    s.close()
+
+
+def test_window_gradient_matches_oracle_and_finite_differences(env):
+    torch, M, AD = env
+    w = I.tiny(600, (4.5, 4.2, 4.8), 21, ntypes=2, g=(0.05, 0.0, 0.0))
+    p = w.params.copy(precision=0)
+    K = 8
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    dev = "cuda"
+    x0 = torch.tensor(w.pos, device=dev, requires_grad=True)
+    v0 = torch.tensor(w.vel, device=dev, requires_grad=True)
+    A = torch.tensor(p.A, device=dev, requires_grad=True)
+    B = torch.tensor(p.B, device=dev, requires_grad=True)
+    G = torch.tensor(p.gamma, device=dev, requires_grad=True)
+    rng = np.random.default_rng(5)
+    cx = torch.tensor(rng.normal(size=w.pos.shape), device=dev)
+    cv = torch.tensor(rng.normal(size=w.pos.shape), device=dev)
+    xk, vk = AD.window(s, p, x0, v0, A, B, G, K, step0=3)
+    loss = (cx * xk).sum() + (cv * vk).sum()
+    loss.backward()
+    # the oracle's chain rule on the same window
+    o = O.Oracle(p, w.pos, w.vel, w.type, w.seed, use_cells=True)
+    o.step = 3
+    o.refresh()
+    ck = OAD.window_forward(o, K)
+    np.testing.assert_allclose(xk.detach().cpu().numpy(), o.x, atol=1e-11)
+    oxb, ovb, otb = OAD.window_vjp(o, ck, cx.cpu().numpy(), cv.cpu().numpy())
+    assert _rel(x0.grad.cpu().numpy(), oxb) < 1e-8
+    assert _rel(v0.grad.cpu().numpy(), ovb) < 1e-8
+    assert _rel(A.grad.cpu().numpy(), otb[0]) < 1e-8
+    assert _rel(B.grad.cpu().numpy(), otb[1]) < 1e-8
+    assert _rel(G.grad.cpu().numpy(), otb[2]) < 1e-8
+
+    # central differences of the GPU forward (kink-free directions)
+    def fwd(xx, vv, AA=A, BB=B, GG=G):
+        with torch.no_grad():
+            a, b = AD.window(s, p, xx, vv, AA, BB, GG, K, step0=3)
+            return float((cx * a).sum() + (cv * b).sum())
+
+    def fd(f, eps):
+        d1 = (f(eps) - f(-eps)) / (2 * eps)
+        d2 = (f(2 * eps) - f(-2 * eps)) / (4 * eps)
+        return d1 if abs(d1 - d2) <= 1e-6 * max(1.0, abs(d1)) else None
+    checked = 0
+    for _ in range(3):
+        dx = torch.tensor(rng.normal(size=w.pos.shape), device=dev)
+        d = fd(lambda e: fwd(x0.detach() + e * dx, v0.detach()), 1e-7)
+        if d is not None:
+            assert abs(d - float((x0.grad * dx).sum())) <= 1e-3 * max(1.0, abs(d))
+            checked += 1
+        dv = torch.tensor(rng.normal(size=w.pos.shape), device=dev)
+        d = fd(lambda e: fwd(x0.detach(), v0.detach() + e * dv), 1e-7)
+        if d is not None:
+            assert abs(d - float((v0.grad * dv).sum())) <= 1e-3 * max(1.0, abs(d))
+            checked += 1
+    for name, T in (("A", A), ("B", B), ("G", G)):
+        E = torch.zeros_like(T)
+        E[0, 1] = E[1, 0] = 1.0
+
+        def f(e, name=name, E=E):
+            kw = {"AA": A.detach(), "BB": B.detach(), "GG": G.detach()}
+            kw["AA" if name == "A" else "BB" if name == "B" else "GG"] = T.detach() + e * E
+            return fwd(x0.detach(), v0.detach(), **kw)
+        d = fd(f, 1e-6)
+        if d is not None:
+            assert abs(d - float(T.grad[0, 1])) <= 1e-3 * max(1.0, abs(d)), (name, d, T.grad[0, 1])
+            checked += 1
+    assert checked >= 4
+    s.close()
