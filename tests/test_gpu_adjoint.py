@@ -112,3 +112,37 @@ def test_window_gradient_matches_oracle_and_finite_differences(env):
             checked += 1
     assert checked >= 4
     s.close()
+
+
+def test_fit_A_B_from_a_target_window(env):
+    """The adjoint drives a fit: from a 10-step window generated with
+    (A, B) = (-40, 25), L-BFGS on |x_K - x_K*|^2 + |v_K - v_K*|^2 with the
+    window gradient recovers A and B when started from (-34, 20)."""
+    torch, M, AD = env
+    w = I.tiny(500, (4.5, 4.5, 4.5), 31)
+    p = w.params.copy(precision=0)
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    dev = "cuda"
+    x0 = torch.tensor(w.pos, device=dev)
+    v0 = torch.tensor(w.vel, device=dev)
+    G = torch.tensor(p.gamma, device=dev)
+    K = 10
+    with torch.no_grad():
+        xt, vt = AD.window(s, p, x0, v0, torch.tensor(p.A, device=dev),
+                           torch.tensor(p.B, device=dev), G, K)
+    theta = torch.tensor([-34.0, 20.0], dtype=torch.float64, device=dev, requires_grad=True)
+    ones = torch.ones((8, 8), dtype=torch.float64, device=dev)
+    opt = torch.optim.LBFGS([theta], lr=1.0, max_iter=60, tolerance_grad=1e-12,
+                            tolerance_change=1e-14, line_search_fn="strong_wolfe")
+
+    def closure():
+        opt.zero_grad()
+        xk, vk = AD.window(s, p, x0, v0, theta[0] * ones, theta[1] * ones, G, K)
+        loss = ((xk - xt) ** 2).sum() + ((vk - vt) ** 2).sum()
+        loss.backward()
+        return loss
+
+    opt.step(closure)
+    a, b = theta.detach().cpu().numpy()
+    assert abs(a - (-40.0)) < 1e-3 * 40 and abs(b - 25.0) < 1e-3 * 25, (a, b)
+    s.close()
