@@ -244,3 +244,56 @@ def tiny(n: int, L, seed: int, periodic=(1, 1, 1), ntypes: int = 1,
     vel = spread * maxwell_velocities(n, p.kT, rng)
     typ = rng.integers(0, ntypes, size=n).astype(np.int32)
     return Workload("tiny", p, pos, vel, typ, seed)
+
+
+def water_slab(seed: int = 1, precision: int = 1, steps: int = 10000) -> Workload:
+    """Water liquid-vacuum slab of Sec. 4.1: periodic box [-50, 50]^3, an fcc
+    slab with lattice constant r_c filling -10 <= x <= 10 (41 planes of 2 x 100
+    x 100 sites: 820,000 particles), A = -50, B = 25, r_d = 0.75, gamma = 12.4,
+    Maxwell velocities at kT = 1."""
+    rng = np.random.default_rng(seed)
+    p = MDPDParams(box_lo=(-50.0, -50.0, -50.0), box=(100.0, 100.0, 100.0),
+                   precision=precision)
+    p.A[:] = -50.0
+    p.B[:] = 25.0
+    p.gamma[:] = 12.4
+    j, k = np.meshgrid(np.arange(100.0), np.arange(100.0), indexing="ij")
+    j = j.ravel()
+    k = k.ravel()
+    planes = []
+    for m in range(41):
+        x = -10.0 + 0.5 * m
+        if m % 2 == 0:
+            yz = [(j, k), (j + 0.5, k + 0.5)]
+        else:
+            yz = [(j + 0.5, k), (j, k + 0.5)]
+        for y, z in yz:
+            planes.append(np.stack([np.full_like(y, x), y - 50.0, z - 50.0], 1))
+    pos = np.concatenate(planes)
+    vel = maxwell_velocities(pos.shape[0], p.kT, rng)
+    return Workload("water_slab", p, pos, vel, np.zeros(pos.shape[0], np.int32), seed,
+                    steps=steps)
+
+
+def contact_slit(A_sl: float, seed: int = 1, precision: int = 1, steps: int = 14000) -> Workload:
+    """Static contact angle set-up of Sec. 4.2: x in [-30, 30] and z in
+    [-2.5, 2.5] periodic, walls for |y| > 4 (solid voxels of 0.5, wall particles
+    at density 35/6 so that the two walls hold about 3,500), 4,000 liquid
+    particles placed at random in -13 <= x <= 13, |y| <= 4, A_LL = -40,
+    A_SL given, B = 25, r_d = 0.75."""
+    rng = np.random.default_rng(seed)
+    lo = (-30.0, -5.0, -2.5)
+    box = (60.0, 10.0, 5.0)
+    p = MDPDParams(box_lo=lo, box=box, periodic=(1, 0, 1), ntypes=2, frozen_types=(1,),
+                   precision=precision)
+    p.set_pair(0, 1, A=A_sl)
+    voxel = 0.5
+    nx, ny, nz = (int(round(b / voxel)) for b in box)
+    yc = lo[1] + (np.arange(ny) + 0.5) * voxel
+    solid_y = np.abs(yc) > 4.0
+    mask = np.broadcast_to(solid_y[None, :, None], (nz, ny, nx)).astype(np.uint8).copy()
+    pos = uniform_positions(4000, (-13.0, -4.0, -2.5), (13.0, 4.0, 2.5), rng)
+    vel = maxwell_velocities(4000, p.kT, rng)
+    return Workload("contact_slit", p, pos, vel, np.zeros(4000, np.int32), seed, mask=mask,
+                    voxel=voxel, origin=lo, wall_density=35.0 / 6.0, shell=1.0, wall_type=1,
+                    wall_seed=seed + 1000, steps=steps)
