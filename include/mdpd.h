@@ -182,12 +182,17 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *                      thread-per-particle density pass; MDPD_KERNELS_SCAN:
  *                      both passes scan the 27 neighbour cells directly.
  *                      Same results up to FP summation order.
+ *   MDPD_OPT_WALL_DENSITY  1: every density pass also accumulates the wall
+ *                      density phi of each mobile particle (Sec. 3.2,
+ *                      Algorithm 1 step 2; read with mdpd_get_wall_density);
+ *                      the thread-per-particle density variant is used while
+ *                      it is on.  0 (default): off.
  *   MDPD_OPT_PROFILE_EVERY  m >= 1: with MDPD_OPT_PROFILE on, record the events
  *                      on every m-th step only (default 1), which keeps their
  *                      cost out of most steps.
  */
 enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3,
-       MDPD_OPT_PROFILE_EVERY = 4 };
+       MDPD_OPT_PROFILE_EVERY = 4, MDPD_OPT_WALL_DENSITY = 5 };
 enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1, MDPD_KERNELS_NLIST_THREAD = 2 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
@@ -199,6 +204,13 @@ enum { MDPD_K_BIN = 0, MDPD_K_DENSITY = 1, MDPD_K_FORCE = 2, MDPD_K_OTHER = 3,
  * recorded; clears the record.  Synchronises. */
 int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps,
                  int64_t* launches);
+
+/* Wall density of the last density pass (MDPD_OPT_WALL_DENSITY on): for each
+ * mobile particle phi_i = sum over frozen particles j with 0 < r_ij < r_c of
+ * 15/(2 pi r_c^3) (1 - r_ij/r_c)^2, the density of solid particles within the
+ * particle's support (Sec. 3.2); 0 for frozen particles.  Host array of N
+ * doubles, id order.  Synchronises. */
+int mdpd_get_wall_density(mdpd_handle* h, double* phi);
 
 /* Replace the parameters of a handle between steps.  Only A, B, gamma, kT, dt,
  * g, frozen_type_mask, xi_dist and rho_self may differ; box, periodicity, rc,

@@ -20,6 +20,8 @@
  *   non-penetration)                                        Sec. 2.2, 3.2
  *   wall particles fill the solid voxels within a shell of given
  *   thickness of the pore space                                   Sec. 2.3
+ *   wall density phi_i of solid particles within a fluid particle's
+ *   support                                         Sec. 3.2, Algorithm 1
  *
  * Where the paper is silent the oracle takes these readings (each is stated
  * again at the code that uses it):
@@ -306,6 +308,45 @@ int orc_density(const orc_sys *s, int64_t n, const double *x, double *rho)
                 if (r2 < rd2) acc += orc_w_rho(sqrt(r2), s->rd);
             }
             rho[i] = acc;
+        }
+        free(lst.j);
+    }
+    if (s->use_cells) cells_free(&c);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wall-particle density, Sec. 3.2 and Algorithm 1 (the phi step): for each   */
+/* fluid (mobile) particle i, the number density of solid (frozen) particles  */
+/* inside its support, phi_i = sum_{j frozen, 0 < r_ij < r_c} w_phi(r_ij),    */
+/* with the density weight of Sec. 2.1 normalised over the support radius r_c */
+/* instead of r_d: w_phi = 15/(2 pi r_c^3) (1 - r/r_c)^2.  phi_i = 0 for      */
+/* frozen i.                                                                  */
+/* ------------------------------------------------------------------------ */
+int orc_wall_density(const orc_sys *s, int64_t n, const double *x,
+                     const int32_t *type, double *phi)
+{
+    orc_cells c = { { 0, 0, 0 }, { 0, 0, 0 }, NULL, NULL };
+    if (s->use_cells && cells_build(s, n, x, &c) != 0) { cells_free(&c); return -1; }
+    const double rc2 = s->rc * s->rc;
+#pragma omp parallel
+    {
+        orc_list lst = { NULL, 0, 0 };
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            double acc = 0.0;
+            if (!is_frozen(s, type[i])) {
+                candidates(s, &c, n, x, i, &lst);
+                for (int64_t k = 0; k < lst.n; ++k) {
+                    int64_t j = lst.j[k];
+                    if (!is_frozen(s, type[j])) continue;
+                    double d[3];
+                    pair_vec(s, &x[3 * i], &x[3 * j], d);
+                    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    if (r2 > 0.0 && r2 < rc2) acc += orc_w_rho(sqrt(r2), s->rc);
+                }
+            }
+            phi[i] = acc;
         }
         free(lst.j);
     }

@@ -59,6 +59,7 @@ def lib():
         _lib.orc_pair_force.argtypes = [P, P, P, i32, i32, d, d, d, P, P]
         _lib.orc_pair_force.restype = C.c_int
         _lib.orc_density.argtypes = [P, i64, P, P]
+        _lib.orc_wall_density.argtypes = [P, i64, P, P, P]
         _lib.orc_forces.argtypes = [P, i64, P, P, P, P, P, u64, P, P]
         _lib.orc_blocked.argtypes = [P, P]
         _lib.orc_observables.argtypes = [P, i64, P, P, P, u64, P]
@@ -200,6 +201,17 @@ class Oracle:
         if lib().orc_density(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(rho)) != 0:
             raise RuntimeError("oracle density failed")
         return rho
+
+    def wall_density(self, x=None) -> np.ndarray:
+        """phi_i: density of frozen particles within r_c of each mobile particle,
+        weight 15/(2 pi r_c^3)(1 - r/r_c)^2 (Sec. 3.2, Algorithm 1); 0 for
+        frozen particles."""
+        x = self.x if x is None else _c(x, np.float64)
+        phi = np.zeros(x.shape[0])
+        if lib().orc_wall_density(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(self.type),
+                                  _ptr(phi)) != 0:
+            raise RuntimeError("oracle wall density failed")
+        return phi
 
     def forces(self, x=None, v=None, rho=None, step=None):
         """Accelerations (m = 1, body force included, frozen = 0) and virial."""

@@ -69,6 +69,8 @@ struct mdpd_handle {
     uint32_t* mask_bits = nullptr;
     uint32_t* nl = nullptr;          // NL_SLOTS * cap neighbour-list entries
     uint32_t* nl_count = nullptr;    // cap
+    void* phi = nullptr;             // cap wall densities (cell order)
+    bool want_phi = false;
     int kernels = MDPD_KERNELS_NLIST;
     bool walls_set = false;
     std::vector<int32_t> h_type;
@@ -159,6 +161,7 @@ void free_particles(mdpd_handle* h)
     dfree(h->type_by_id);
     dfree(h->nl);
     dfree(h->nl_count);
+    dfree(h->phi);
 }
 
 int alloc_particles(mdpd_handle* h, int64_t cap)
@@ -188,6 +191,7 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
     if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->nl_count, c * sizeof(uint32_t));
+    if (!rc) rc = dalloc(h, &h->phi, c * tsz);
     if (!rc) h->cap = (int64_t)c;
     return rc;
 }
@@ -216,6 +220,7 @@ void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
     std::swap(a->type_by_id, b->type_by_id);
     std::swap(a->nl, b->nl);
     std::swap(a->nl_count, b->nl_count);
+    std::swap(a->phi, b->phi);
     std::swap(a->cap, b->cap);
 }
 
@@ -362,7 +367,11 @@ void enqueue_bin(mdpd_handle* h, bool gather_a)
 
 void enqueue_density(mdpd_handle* h)
 {
-    if (h->kernels == MDPD_KERNELS_NLIST)
+    h->ph.phi_out = h->want_phi ? h->phi : nullptr;
+    if (h->want_phi)              // the wall density is accumulated by this variant only
+        launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
+                          h->cell_s, h->start, h->rho, h->nl, h->nl_count);
+    else if (h->kernels == MDPD_KERNELS_NLIST)
         launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph,
                             h->pos4, h->start, h->rho, h->nl, h->nl_count);
     else if (h->kernels == MDPD_KERNELS_NLIST_THREAD)
@@ -976,6 +985,11 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         h->prof_tick = 0;
         return MDPD_OK;
     }
+    case MDPD_OPT_WALL_DENSITY:
+        CK(cudaStreamSynchronize(h->stream));
+        h->want_phi = value != 0;
+        destroy_graphs(h);
+        return MDPD_OK;
     case MDPD_OPT_PROFILE_EVERY:
         if (value < 1) return h->fail(MDPD_ERR_INVALID_ARG, "profile interval must be >= 1");
         h->prof_every = value;
@@ -1087,6 +1101,19 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
         CK(cudaMemcpy(theta_bar, t, sizeof(t), cudaMemcpyHostToDevice));
     }
     return MDPD_OK;
+}
+
+int mdpd_get_wall_density(mdpd_handle* h, double* phi)
+{
+    if (!h || !phi) return MDPD_ERR_INVALID_ARG;
+    if (!h->want_phi) return h->fail(MDPD_ERR_INVALID_ARG, "MDPD_OPT_WALL_DENSITY is off");
+    int rc = sync_check(h);
+    if (rc) return rc;
+    double* tmp = h->v[1 - h->cur];
+    launch_scatter_scalar_by_id(h->stream, h->precision, (int)h->n, h->id[h->cur], h->phi, tmp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(phi, tmp, (size_t)h->n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    return sync_check(h);
 }
 
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)

@@ -44,7 +44,14 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const auto pi = pos4[s];
-    const bool mobile = ph.list_all || ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+    const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+    const bool mobile = ph.list_all || mob_true;
+    // wall density of a mobile particle: sum over frozen partners within r_c of
+    // 15/(2 pi r_c^3) (1 - r/r_c)^2
+    const bool want_phi = ph.phi_out != nullptr && mob_true;
+    const T inv_rc = (T)(1.0 / ph.rc);
+    const T cphi = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rc * ph.rc * ph.rc));
+    T phi = T(0);
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
     T acc = ph.rho_self ? cw : T(0);
@@ -76,6 +83,10 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                     if (other && mobile && r2 < rc2 && r2 > T(0)) {
                         if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
                         ++cnt;
+                        if (want_phi && ((ph.frozen >> unpack_u32(pj.w)) & 1u)) {
+                            const T wq = T(1) - sqrt_t(r2) * inv_rc;
+                            phi += cphi * wq * wq;
+                        }
                     }
                 }
             }
@@ -83,6 +94,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     }
     rho_out[s] = acc;
     nl_count[s] = cnt;
+    if (ph.phi_out) ((T*)ph.phi_out)[s] = phi;
 }
 
 // Warp-cooperative density pass: one warp per home cell.  The 27 neighbour

@@ -35,6 +35,7 @@ struct Phys {
     int xi_dist;
     int rho_self;
     int list_all;                 // 1: the density pass lists partners of frozen particles too
+    void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
     double A[64], B[64], gamma[64], sigma[64];
 };

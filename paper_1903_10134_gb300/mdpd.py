@@ -24,6 +24,7 @@ OPT_GRAPH = 1
 OPT_PROFILE = 2
 OPT_KERNELS = 3
 OPT_PROFILE_EVERY = 4
+OPT_WALL_DENSITY = 5
 KERNELS_NLIST = 0
 KERNELS_SCAN = 1
 KERNELS_NLIST_THREAD = 2
@@ -93,7 +94,7 @@ SYMBOLS = (
     "mdpd_observables", "mdpd_observables_mean", "mdpd_pair_count", "mdpd_set_option",
     "mdpd_profile",
     "mdpd_describe", "mdpd_autotune", "mdpd_set_params", "mdpd_set_step",
-    "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_density_noalloc", "mdpd_destroy",
+    "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error",
 )
 
@@ -134,6 +135,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_density_noalloc.argtypes = [P, i64, P, P, P]
     L.mdpd_autotune.argtypes = [P, i32, C.POINTER(i32), P]
     L.mdpd_set_params.argtypes = [P, P]
+    L.mdpd_get_wall_density.argtypes = [P, P]
     L.mdpd_set_step.argtypes = [P, i64]
     L.mdpd_get_accel_dev.argtypes = [P, P]
     L.mdpd_force_vjp_dev.argtypes = [P, P, P, P, P]
@@ -315,6 +317,12 @@ def mdpd_describe(h):
     return nc.tolist(), int(lps.value)
 
 
+def mdpd_get_wall_density(h) -> np.ndarray:
+    phi = np.zeros(mdpd_num_particles(h))
+    _check(lib().mdpd_get_wall_density(h, _p(phi)), h)
+    return phi
+
+
 def mdpd_set_params(h, params):
     cp = to_c_params(params)
     _check(lib().mdpd_set_params(h, C.byref(cp)), h)
@@ -416,6 +424,9 @@ class System:
 
     def profile(self):
         return mdpd_profile(self.h)
+
+    def wall_density(self):
+        return mdpd_get_wall_density(self.h)
 
     def autotune(self, reps: int = 5):
         return mdpd_autotune(self.h, reps)

@@ -310,3 +310,47 @@ def test_sampled_profile_counts(M):
     assert launches == 20 * lps + 1
     assert all(v > 0 for v in prof.values())
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["slit", "rock"])
+def test_wall_density_matches_oracle(M, name, precision):
+    """Wall-particle density phi (Sec. 3.2, Algorithm 1) accumulated in the
+    density pass: equal to the oracle's on the same positions (FP64 1e-12,
+    FP32 2e-5 (1 + phi)); the option changes nothing else (the trajectory is
+    bit-identical with it on and off, on the same density variant), and reading
+    phi with it off is an error."""
+    if name == "slit":
+        w = I.slit(Lx=6.0, Ly=6.0, H=6.0, wall=1.0, voxel=0.5, g=0.2, seed=3, precision=precision)
+    else:
+        w = I.rock(nvox=32, voxel=0.5, corr=4.0, porosity=0.3, g=0.5, seed=5, precision=precision)
+    s_on = M.System.from_workload(w, precision=precision)
+    s_off = M.System.from_workload(w, precision=precision)
+    # phi rides on the thread-per-particle density pass: compare with that variant
+    s_off.set_option(M.OPT_KERNELS, M.KERNELS_NLIST_THREAD)
+    with pytest.raises(M.MDPDError):
+        s_on.wall_density()
+    s_on.set_option(M.OPT_WALL_DENSITY, 1)
+    tol = 1e-12 if precision == 0 else 2e-5
+    for k in range(3):
+        if k == 0:
+            s_on.forces()
+        else:
+            s_on.step(7)
+            s_off.step(7)
+        phi = s_on.wall_density()
+        x, v, t, _ = s_on.state()
+        o = O.Oracle(w.params.copy(precision=0), x, v, t, w.seed, use_cells=True)
+        ref = o.wall_density()
+        assert np.all(ref[t == w.wall_type] == 0) and np.all(phi[t == w.wall_type] == 0)
+        assert ref[t != w.wall_type].max() > 1.0          # particles do sit near walls
+        assert np.all(np.abs(phi - ref) <= tol * (1 + np.abs(ref))), np.abs(phi - ref).max()
+        if k > 0:
+            xo, vo, _, _ = s_off.state()
+            assert np.array_equal(x, xo) and np.array_equal(v, vo)
+    s_on.set_option(M.OPT_WALL_DENSITY, 0)
+    s_on.step(1)
+    with pytest.raises(M.MDPDError):
+        s_on.wall_density()
+    s_on.close()
+    s_off.close()
