@@ -5,7 +5,7 @@ One bench step = one velocity-Verlet time step of the whole hot path (binning,
 density pass, force pass fused with the half-kicks, drift and reflection, FP64
 reductions) over the synthetic workload.  Prints one JSON line.
 
-  python bench.py [--gpus N --steps K --warmup W] [--workload slab|bulk|slit|rock]
+  python bench.py [--gpus N --steps K --warmup W] [--workload slab|bulk|slit|rock|batch]
                   [--precision fp32|fp64] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the reference arm of this
@@ -47,6 +47,9 @@ DESC = {
             "(voxel 0.5, 1 rc shell at density 6, A_fs=-30), g_x=0.02, fluid density 6",
     "rock": "synthetic porous rock, 256^3 voxel Gaussian random field (corr 4 voxels) at "
             "porosity 0.15, voxel 0.5 rc, 1 rc wall shell at density 6, fluid density 6, g_x=0.01",
+    "batch": "256 independent liquid slabs in one batch (one launch per kernel for all), "
+             "N_r ~ U[2000,20000] (2.94M in all), A_r ~ U[-50,-30], B_r ~ U[15,35], "
+             "box 3L x L x L with L = (N_r/6)^(1/3), liquid middle third at density 6",
 }
 
 
@@ -60,6 +63,8 @@ def make_workload(name: str, precision: int, seed: int, nvox: int = 256):
         return I.slit(seed=seed, precision=precision)
     if name == "rock":
         return I.rock(nvox=nvox, seed=seed, precision=precision)
+    if name == "batch":
+        return I.batch_slabs(nrep=256, seed=seed, precision=precision)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -142,6 +147,24 @@ def oracle_throughput(w, budget_s: float, max_steps: int = 1000):
             "cores": O.num_threads(), "n": o.n}
 
 
+def oracle_throughput_batch(ws, budget_s: float):
+    """The FP64 oracle on a batch: one step of replica after replica (each a
+    system of its own, as the oracle has no batching) until about budget_s
+    seconds are spent; particle-steps/s over the replicas done."""
+    from oracle import oracle as O
+    done_n, el, k = 0, 0.0, 0
+    while k < len(ws) and (k == 0 or el < budget_s):
+        w = ws[k]
+        o = O.Oracle(w.params.copy(), w.pos, w.vel, w.type, w.seed, use_cells=True)
+        t0 = time.perf_counter()
+        o.run(1)
+        el += time.perf_counter() - t0
+        done_n += o.n
+        k += 1
+    return {"value": done_n / el, "steps": 1, "replicas": k, "seconds": el,
+            "cores": O.num_threads(), "n": done_n}
+
+
 def _oracle_walls(w) -> dict:
     """Wall particles and mask for the oracle (its own packing of the image)."""
     if w.mask is None:
@@ -192,6 +215,24 @@ def run_reference(args):
         return
     from oracle import oracle as O
     w = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
+    if args.workload == "batch":
+        info = oracle_throughput_batch(w, args.ref_seconds)
+        value = info["value"]
+        sample = (f"one FP64 oracle step of each of the first {info['replicas']} of "
+                  f"{len(w)} replicas ({info['n']} particles), {info['seconds']:.1f} s")
+        print(json.dumps({
+            "impl": "reference", "metric": "particle-steps/s", "value": value,
+            "unit": "particle-steps/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(x.n for x in w) / value,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": DESC[args.workload],
+                       "n": sum(x.n for x in w), "precision": "fp64"},
+            "cpu_baseline": {"value": value, "unit": "particle-steps/s",
+                             "cores": info["cores"], "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return
     walls = _oracle_walls(w)
     o = O.Oracle(w.params.copy(), w.pos, w.vel, w.type, w.seed, use_cells=True, **walls)
     t0 = time.perf_counter()
@@ -265,7 +306,10 @@ def run_ours(args):
     prec = 0 if args.precision == "fp64" else 1
     w = make_workload(args.workload, prec, seed=replica_seed(rank), nvox=args.nvox)
     stream = torch.cuda.Stream()
-    s = mdpd.System.from_workload(w, stream=stream)
+    if args.workload == "batch":
+        s = mdpd.Batch.from_workloads(w, stream=stream)
+    else:
+        s = mdpd.System.from_workload(w, stream=stream)
     tuned = None
     if args.kernels == "auto":
         chosen, tms = s.autotune()
@@ -365,11 +409,16 @@ def run_ours(args):
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
-            info = oracle_throughput(wc, args.cpu_seconds, max_steps=200)
+            if args.workload == "batch":
+                info = oracle_throughput_batch(wc, args.cpu_seconds)
+                sample = (f"one FP64 oracle step of each of the first {info['replicas']} of "
+                          f"{len(wc)} replicas ({info['n']} particles), {info['seconds']:.1f} s")
+            else:
+                info = oracle_throughput(wc, args.cpu_seconds, max_steps=200)
+                sample = (f"{info['steps']} FP64 oracle steps of the full {args.workload} "
+                          f"workload (N={info['n']}), {info['seconds']:.1f} s")
             cpu = {"value": info["value"], "unit": "particle-steps/s", "cores": info["cores"],
-                   "kind": "oracle",
-                   "sample": f"{info['steps']} FP64 oracle steps of the full {args.workload} "
-                             f"workload (N={info['n']}), {info['seconds']:.1f} s"}
+                   "kind": "oracle", "sample": sample}
         line = {
             "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -377,6 +426,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32" if prec == 1 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "desc": DESC[args.workload], "n": n,
                        "nvox": args.nvox if args.workload == "rock" else None,
+                       "replicas": len(w) if args.workload == "batch" else None,
                        "precision": args.precision, "kernels": args.kernels, "autotune": tuned,
                        "l2": "flushed between timed steps" if flush else "working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

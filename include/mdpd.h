@@ -36,6 +36,7 @@ extern "C" {
 
 #define MDPD_MAX_TYPES 8
 #define MDPD_NUM_OBS 16
+#define MDPD_MAX_REPLICAS 65536
 
 enum {
     MDPD_OK = 0,
@@ -94,6 +95,45 @@ int mdpd_create(const mdpd_params* params, int64_t n, const double* pos,
 int mdpd_create_dev(const mdpd_params* params, int64_t n, const double* pos,
                     const double* vel, const int32_t* type, uint64_t seed,
                     void* cuda_stream, mdpd_handle** out);
+
+/* Batch of nrep independent systems advanced together: every kernel of a
+ * time step is one launch over all replicas (ensembles, parameter sweeps and
+ * fits of A, B over many small boxes; the paper's single system is the case
+ * nrep = 1).  Replica r has its own params[r] (box, periodicity, pair
+ * tables, r_c, r_d, dt, kT, body force; precision must be equal), its own
+ * seed seeds[r] and n[r] particles; the inputs pos, vel (3 N doubles), type
+ * (N values), N = sum n[r], hold replica 0's particles first, then replica
+ * 1's, and so on, and the batch's particle ids follow that order.  Within a
+ * replica the random stream is keyed on the particle's index inside the
+ * replica, so replica r evolves bit-identically to mdpd_create() of
+ * (params[r], n[r] particles, seeds[r]) run alone with the same kernel
+ * variant.  Walls, the force VJP and the wall density are not available on a
+ * batch handle.  mdpd_step, mdpd_get_state/set_state(_dev), mdpd_forces(_dev),
+ * mdpd_set_step, mdpd_sync, mdpd_pair_count (summed over replicas),
+ * mdpd_profile, mdpd_set_option and mdpd_autotune apply to the whole batch;
+ * the observables are per replica (mdpd_batch_observables).
+ * Errors: INVALID_ARG (nrep outside 1..MDPD_MAX_REPLICAS, any replica's
+ * params invalid as for mdpd_create, mixed precision, more than 2^27
+ * particles or 16.7M cells in all), OOM, CUDA. */
+int mdpd_create_batch(int32_t nrep, const mdpd_params* params, const int64_t* n,
+                      const double* pos, const double* vel, const int32_t* type,
+                      const uint64_t* seeds, void* cuda_stream, mdpd_handle** out);
+
+/* Number of replicas (1 for a handle made by mdpd_create). */
+int mdpd_num_replicas(const mdpd_handle* h, int32_t* nrep);
+
+/* Per-replica observables of a batch handle, nrep * MDPD_NUM_OBS doubles
+ * (replica-major, each record laid out as mdpd_observables): the last step's
+ * values (mean = 0) or the running means since the last reset (mean = 1;
+ * reset = 1 then clears the running sums).  INVALID_ARG on a single-system
+ * handle.  Synchronises. */
+int mdpd_batch_observables(mdpd_handle* h, double* out, int32_t mean, int32_t reset);
+
+/* Replace every replica's parameters between steps (params: nrep records).
+ * The boxes, periodicity, r_c, precision and ntypes must not change; the
+ * seeds are kept.  Captured step graphs stay valid.  INVALID_ARG on a
+ * single-system handle.  Synchronises. */
+int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params);
 
 /* Walls from a voxel image (Sec. 2.2, 2.3).  solid: nx*ny*nz bytes, x
  * fastest, nonzero = solid, covering [origin, origin + n*voxel) per axis.

@@ -2,6 +2,7 @@
 // system, validates arguments, enqueues the kernels of a time step on the
 // handle's stream (directly or as a captured CUDA graph) and moves data in
 // and out in particle-id order.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@ namespace {
 constexpr int64_t MAX_PARTICLES = int64_t(1) << 27;   // neighbour-list entries hold j << 5
 constexpr int64_t MAX_SCAN = int64_t(4096) * 4096;   // limit of the two-level scan
 constexpr int EV_PER_STEP = 5;                        // profile events per step
+constexpr int PAIR_BLOCK_WARPS = 4;                   // observable partials per force block
 
 std::string g_create_error;
 
@@ -86,6 +88,29 @@ struct mdpd_handle {
     int64_t prof_every = 1, prof_tick = 0;   // record events on every prof_every-th step
     std::vector<cudaEvent_t> prof_ev;
     int64_t prof_launches = 0;
+
+    // batch of independent replicas (nrep > 0; see Batch): host records,
+    // device records and chunk tables, per-replica observable records
+    int nrep = 0;
+    std::vector<Rep> reps;
+    std::vector<mdpd_params> rep_p;
+    Rep* d_reps = nullptr;
+    int4* d_chunks = nullptr;
+    int4* d_cchunks = nullptr;
+    int2* d_wr = nullptr;
+    double* obs_b = nullptr;
+    int nchunk = 0, ncchunk = 0;
+
+    Batch batch() const
+    {
+        Batch b;
+        b.reps = d_reps;
+        b.chunks = d_chunks;
+        b.cchunks = d_cchunks;
+        b.nchunk = nchunk;
+        b.ncchunk = ncchunk;
+        return b;
+    }
 
     std::string err;
 
@@ -185,7 +210,8 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->slot, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->key, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->src, c * sizeof(uint32_t));
-    if (!rc) rc = dalloc(h, &h->partials, (size_t)obs_num_partials((int)c) * OBS_PARTIALS * sizeof(double));
+    const size_t nparts = std::max((size_t)obs_num_partials((int)c), (size_t)h->nchunk * (PAIR_BLOCK_WARPS));
+    if (!rc) rc = dalloc(h, &h->partials, nparts * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->red_l1, (size_t)(reduce_l1_blocks(obs_num_partials((int)c)) + 1) * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
@@ -275,10 +301,8 @@ int validate_params(const mdpd_params* p, std::string& why)
     return MDPD_OK;
 }
 
-void setup_geo_phys(mdpd_handle* h)
+void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
 {
-    const mdpd_params& p = h->p;
-    Geo& g = h->geo;
     g.ncell = 1;
     for (int k = 0; k < 3; ++k) {
         int m = (int)std::floor(p.box[k] / p.rc);
@@ -292,7 +316,6 @@ void setup_geo_phys(mdpd_handle* h)
         g.inv_h[k] = 1.0 / g.h[k];
         g.ncell *= m;
     }
-    Phys& f = h->ph;
     f.rc = p.rc;
     f.rd = p.rd;
     f.dt = p.dt;
@@ -303,8 +326,8 @@ void setup_geo_phys(mdpd_handle* h)
     f.ntypes = p.ntypes;
     f.xi_dist = p.xi_dist;
     f.rho_self = p.rho_self ? 1 : 0;
-    f.key0 = (uint32_t)h->seed;
-    f.key1 = (uint32_t)(h->seed >> 32);
+    f.key0 = (uint32_t)seed;
+    f.key1 = (uint32_t)(seed >> 32);
     for (int a = 0; a < 8; ++a)
         for (int b = 0; b < 8; ++b) {
             f.A[a * 8 + b] = p.A[a][b];
@@ -312,6 +335,15 @@ void setup_geo_phys(mdpd_handle* h)
             f.gamma[a * 8 + b] = p.gamma[a][b];
             f.sigma[a * 8 + b] = std::sqrt(2.0 * p.gamma[a][b] * p.kT);
         }
+}
+
+void setup_geo_phys(mdpd_handle* h)
+{
+    const int list_all = h->ph.list_all;
+    h->geo = Geo{};
+    h->ph = Phys{};
+    make_geo_phys(h->p, h->seed, h->geo, h->ph);
+    h->ph.list_all = list_all;
 }
 
 int status_to_code(uint32_t st)
@@ -356,17 +388,36 @@ void enqueue_bin(mdpd_handle* h, bool gather_a)
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
     // count[] is zero here: cleared at creation and by every cell sort
-    launch_bin_count(st, n, h->cap, h->x[h->cur], h->geo, h->cellof, h->slot, h->count, h->status);
+    if (h->nrep)
+        launch_bin_count_batch(st, h->cap, h->x[h->cur], h->batch(), h->cellof, h->slot, h->count,
+                               h->status);
+    else
+        launch_bin_count(st, n, h->cap, h->x[h->cur], h->geo, h->cellof, h->slot, h->count,
+                         h->status);
     launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp);
     launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src);
     launch_cell_sort(st, h->geo.ncell, h->start, h->key, h->src, h->count);
-    launch_gather(st, h->precision, n, h->cap, h->src, h->cellof, master(h, h->cur),
-                  master(h, 1 - h->cur), gather_a, h->geo, h->pos4, h->vel4, h->cell_s);
+    if (h->nrep)
+        launch_gather_batch(st, h->precision, h->cap, h->src, h->cellof, master(h, h->cur),
+                            master(h, 1 - h->cur), gather_a, h->batch(), h->pos4, h->vel4,
+                            h->cell_s);
+    else
+        launch_gather(st, h->precision, n, h->cap, h->src, h->cellof, master(h, h->cur),
+                      master(h, 1 - h->cur), gather_a, h->geo, h->pos4, h->vel4, h->cell_s);
     h->cur = 1 - h->cur;
 }
 
 void enqueue_density(mdpd_handle* h)
 {
+    if (h->nrep) {
+        if (h->kernels == MDPD_KERNELS_NLIST)
+            launch_density_cell_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
+                                      h->start, h->rho, h->nl, h->nl_count);
+        else
+            launch_density_nl_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
+                                    h->cell_s, h->start, h->rho, h->nl, h->nl_count);
+        return;
+    }
     h->ph.phi_out = h->want_phi ? h->phi : nullptr;
     if (h->want_phi)              // the wall density is accumulated by this variant only
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
@@ -384,7 +435,11 @@ void enqueue_density(mdpd_handle* h)
 
 void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 {
-    if (h->kernels != MDPD_KERNELS_SCAN)
+    if (h->nrep)
+        launch_force_nl_batch(h->stream, h->precision, mode, h->cap, h->batch(), h->pos4, h->vel4,
+                              h->rho, h->cell_s, h->start, h->nl, h->nl_count, h->step,
+                              step_offset, master(h, h->cur), out, h->partials, h->status);
+    else if (h->kernels != MDPD_KERNELS_SCAN)
         launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
                         h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->nl, h->nl_count,
                         h->step, step_offset, master(h, h->cur), out, h->partials, h->status);
@@ -396,6 +451,11 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 
 void enqueue_reduce(mdpd_handle* h, int advance)
 {
+    if (h->nrep) {
+        launch_reduce_obs_batch(h->stream, h->partials, h->nchunk * PAIR_BLOCK_WARPS, h->d_wr,
+                                h->nrep, h->red_ticket, h->obs_b, h->step, advance);
+        return;
+    }
     launch_reduce_obs(h->stream, h->partials, obs_num_partials((int)h->n), h->red_l1,
                       h->red_ticket, h->obs, h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS,
                       h->step, advance);
@@ -515,31 +575,16 @@ int check_ptr_kind(mdpd_handle* h, const void* p, bool want_device)
     return MDPD_OK;
 }
 
-int create_common(const mdpd_params* params, int64_t n, const double* pos, const double* vel,
-                  const int32_t* type, uint64_t seed, void* stream, mdpd_handle** out,
-                  bool device_inputs)
+// Device setup shared by single systems and batches: stream, type check
+// (particle i of replica r must have a type below ntypes[r]; replica r holds
+// the ids [bounds[r], bounds[r + 1])), allocations, upload, loading and the
+// first force evaluation.  Owns h: destroys it on failure.
+int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int32_t* type,
+                void* stream, bool device_inputs, const std::vector<int64_t>& bounds,
+                const std::vector<int>& ntypes, mdpd_handle** out)
 {
-    g_create_error.clear();
-    if (!out) { g_create_error = "out is NULL"; return MDPD_ERR_INVALID_ARG; }
-    *out = nullptr;
-    std::string why;
-    int rc = validate_params(params, why);
-    if (rc) { g_create_error = why; return rc; }
-    if (n < 0 || n > MAX_PARTICLES) { g_create_error = "n out of range"; return MDPD_ERR_INVALID_ARG; }
-    if (n > 0 && (!pos || !vel || !type)) { g_create_error = "pos, vel and type are required"; return MDPD_ERR_INVALID_ARG; }
-    if (!device_inputs)
-        for (int64_t i = 0; i < n; ++i)
-            if (type[i] < 0 || type[i] >= params->ntypes) {
-                g_create_error = "type out of range at particle " + std::to_string(i);
-                return MDPD_ERR_INVALID_ARG;
-            }
-
-    mdpd_handle* h = new mdpd_handle();
-    h->p = *params;
-    h->seed = seed;
-    h->precision = params->precision;
-    h->n = h->n_user = n;
-    setup_geo_phys(h);
+    const int64_t n = h->n;
+    int rc;
     auto bail = [&](int code) {
         g_create_error = h->err;
         mdpd_destroy(h);
@@ -579,11 +624,12 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
         } else {
             std::memcpy(h->h_type.data(), type, (size_t)n * sizeof(int32_t));
         }
-        for (int64_t i = 0; i < n; ++i)
-            if (h->h_type[i] < 0 || h->h_type[i] >= params->ntypes) {
-                h->err = "type out of range at particle " + std::to_string(i);
-                return bail(MDPD_ERR_INVALID_ARG);
-            }
+        for (size_t r = 0; r + 1 < bounds.size(); ++r)
+            for (int64_t i = bounds[r]; i < bounds[r + 1]; ++i)
+                if (h->h_type[i] < 0 || h->h_type[i] >= ntypes[r]) {
+                    h->err = "type out of range at particle " + std::to_string(i);
+                    return bail(MDPD_ERR_INVALID_ARG);
+                }
     }
     if ((rc = alloc_particles(h, n))) return bail(rc);
     const int64_t nb = scan_num_blocks(h->geo.ncell);
@@ -620,12 +666,139 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
         return bail(MDPD_ERR_CUDA);
     }
     h->cur = 0;
-    launch_load_state(st, (int)n, h->cap, h->fout, h->x[1], h->geo, master(h, 0), h->type_by_id,
-                      h->status);
+    if (h->nrep)
+        launch_load_state_batch(st, h->cap, h->fout, h->x[1], h->batch(), master(h, 0),
+                                h->type_by_id, h->status);
+    else
+        launch_load_state(st, (int)n, h->cap, h->fout, h->x[1], h->geo, master(h, 0),
+                          h->type_by_id, h->status);
     if ((rc = evaluate(h, nullptr, false))) return bail(rc);
     if ((rc = sync_check(h))) return bail(rc);
     *out = h;
     return MDPD_OK;
+}
+
+int create_common(const mdpd_params* params, int64_t n, const double* pos, const double* vel,
+                  const int32_t* type, uint64_t seed, void* stream, mdpd_handle** out,
+                  bool device_inputs)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return MDPD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    std::string why;
+    int rc = validate_params(params, why);
+    if (rc) { g_create_error = why; return rc; }
+    if (n < 0 || n > MAX_PARTICLES) { g_create_error = "n out of range"; return MDPD_ERR_INVALID_ARG; }
+    if (n > 0 && (!pos || !vel || !type)) { g_create_error = "pos, vel and type are required"; return MDPD_ERR_INVALID_ARG; }
+    if (!device_inputs)
+        for (int64_t i = 0; i < n; ++i)
+            if (type[i] < 0 || type[i] >= params->ntypes) {
+                g_create_error = "type out of range at particle " + std::to_string(i);
+                return MDPD_ERR_INVALID_ARG;
+            }
+
+    mdpd_handle* h = new mdpd_handle();
+    h->p = *params;
+    h->seed = seed;
+    h->precision = params->precision;
+    h->n = h->n_user = n;
+    setup_geo_phys(h);
+    return init_handle(h, pos, vel, type, stream, device_inputs, { 0, n }, { params->ntypes }, out);
+}
+
+// Batch of nrep independent systems: replica r has its own parameters, seed
+// and n[r] particles (the ids [sum_{q<r} n[q], ... + n[r]) of the inputs); its
+// cells follow those of replica r - 1 in one lattice, so one launch of each
+// kernel advances every replica.
+int create_batch(int32_t nrep, const mdpd_params* params, const int64_t* n, const double* pos,
+                 const double* vel, const int32_t* type, const uint64_t* seeds, void* stream,
+                 mdpd_handle** out)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "out is NULL"; return MDPD_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (nrep < 1 || nrep > MDPD_MAX_REPLICAS || !params || !n || !seeds) {
+        g_create_error = "nrep must be in 1..MDPD_MAX_REPLICAS with params, n and seeds given";
+        return MDPD_ERR_INVALID_ARG;
+    }
+    std::vector<int64_t> bounds(1, 0);
+    std::vector<int> ntypes;
+    int64_t cells = 0;
+    for (int r = 0; r < nrep; ++r) {
+        std::string why;
+        int rc = validate_params(&params[r], why);
+        if (rc) { g_create_error = "replica " + std::to_string(r) + ": " + why; return rc; }
+        if (params[r].precision != params[0].precision) {
+            g_create_error = "all replicas must have the same precision";
+            return MDPD_ERR_INVALID_ARG;
+        }
+        if (n[r] < 0 || bounds.back() + n[r] > MAX_PARTICLES) {
+            g_create_error = "particle counts out of range";
+            return MDPD_ERR_INVALID_ARG;
+        }
+        bounds.push_back(bounds.back() + n[r]);
+        ntypes.push_back(params[r].ntypes);
+    }
+    const int64_t ntot = bounds.back();
+    if (ntot > 0 && (!pos || !vel || !type)) { g_create_error = "pos, vel and type are required"; return MDPD_ERR_INVALID_ARG; }
+
+    mdpd_handle* h = new mdpd_handle();
+    h->nrep = nrep;
+    h->p = params[0];
+    h->seed = seeds[0];
+    h->precision = params[0].precision;
+    h->n = h->n_user = ntot;
+    h->kernels = MDPD_KERNELS_NLIST;
+    h->rep_p.assign(params, params + nrep);
+    h->reps.resize((size_t)nrep);
+    std::vector<int4> chunks, cchunks;
+    std::vector<int2> wr((size_t)nrep);
+    for (int r = 0; r < nrep; ++r) {
+        Rep& R = h->reps[r];
+        R = Rep{};
+        make_geo_phys(params[r], seeds[r], R.geo, R.ph);
+        R.cell0 = cells;
+        R.id0 = (uint32_t)bounds[r];
+        R.n = (uint32_t)n[r];
+        cells += R.geo.ncell;
+        if (cells > MAX_SCAN) {
+            delete h;
+            g_create_error = "too many cells in the batch (more than 16.7M)";
+            return MDPD_ERR_INVALID_ARG;
+        }
+        wr[r].x = (int)chunks.size() * PAIR_BLOCK_WARPS;
+        for (int64_t f = bounds[r]; f < bounds[r + 1]; f += BATCH_CHUNK)
+            chunks.push_back(make_int4(r, (int)f, (int)std::min<int64_t>(BATCH_CHUNK, bounds[r + 1] - f), 0));
+        wr[r].y = (int)chunks.size() * PAIR_BLOCK_WARPS;
+        for (int64_t c = R.cell0; c < R.cell0 + R.geo.ncell; c += BATCH_CELL_CHUNK)
+            cchunks.push_back(make_int4(r, (int)c, (int)std::min<int64_t>(BATCH_CELL_CHUNK, R.cell0 + R.geo.ncell - c), 0));
+    }
+    h->geo = h->reps[0].geo;
+    h->geo.ncell = cells;                  // the concatenated lattice (scan and cell sort)
+    h->ph = h->reps[0].ph;
+    h->nchunk = (int)chunks.size();
+    h->ncchunk = (int)cchunks.size();
+    int rc;
+    if ((rc = dalloc(h, &h->d_reps, sizeof(Rep) * (size_t)nrep)) ||
+        (rc = dalloc(h, &h->d_chunks, sizeof(int4) * chunks.size())) ||
+        (rc = dalloc(h, &h->d_cchunks, sizeof(int4) * cchunks.size())) ||
+        (rc = dalloc(h, &h->d_wr, sizeof(int2) * wr.size())) ||
+        (rc = dalloc(h, &h->obs_b, sizeof(double) * OBS_STRIDE * (size_t)nrep))) {
+        g_create_error = h->err;
+        mdpd_destroy(h);
+        return rc;
+    }
+    bool ok = cudaMemcpy(h->d_reps, h->reps.data(), sizeof(Rep) * (size_t)nrep, cudaMemcpyHostToDevice) == cudaSuccess &&
+              (chunks.empty() || cudaMemcpy(h->d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
+              (cchunks.empty() || cudaMemcpy(h->d_cchunks, cchunks.data(), sizeof(int4) * cchunks.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
+              cudaMemcpy(h->d_wr, wr.data(), sizeof(int2) * wr.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+              cudaMemset(h->obs_b, 0, sizeof(double) * OBS_STRIDE * (size_t)nrep) == cudaSuccess;
+    if (!ok) {
+        g_create_error = "batch tables upload failed";
+        mdpd_destroy(h);
+        return MDPD_ERR_CUDA;
+    }
+    return init_handle(h, pos, vel, type, stream, false, bounds, ntypes, out);
 }
 
 }  // namespace
@@ -649,11 +822,82 @@ int mdpd_create_dev(const mdpd_params* params, int64_t n, const double* pos, con
     return create_common(params, n, pos, vel, type, seed, cuda_stream, out, true);
 }
 
+int mdpd_create_batch(int32_t nrep, const mdpd_params* params, const int64_t* n,
+                      const double* pos, const double* vel, const int32_t* type,
+                      const uint64_t* seeds, void* cuda_stream, mdpd_handle** out)
+{
+    return create_batch(nrep, params, n, pos, vel, type, seeds, cuda_stream, out);
+}
+
+int mdpd_num_replicas(const mdpd_handle* h, int32_t* nrep)
+{
+    if (!h || !nrep) return MDPD_ERR_INVALID_ARG;
+    *nrep = h->nrep ? h->nrep : 1;
+    return MDPD_OK;
+}
+
+int mdpd_batch_observables(mdpd_handle* h, double* out, int32_t mean, int32_t reset)
+{
+    if (!h || !out) return MDPD_ERR_INVALID_ARG;
+    if (!h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "not a batch handle");
+    int rc = sync_check(h);
+    if (rc) return rc;
+    std::vector<double> buf((size_t)h->nrep * OBS_STRIDE);
+    CK(cudaMemcpy(buf.data(), h->obs_b, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < h->nrep; ++r) {
+        const double* b = &buf[(size_t)r * OBS_STRIDE];
+        const double cnt = b[2 * MDPD_NUM_OBS];
+        for (int k = 0; k < MDPD_NUM_OBS; ++k)
+            out[(size_t)r * MDPD_NUM_OBS + k] =
+                mean ? (cnt > 0 ? b[MDPD_NUM_OBS + k] / cnt : 0.0) : b[k];
+    }
+    if (mean && reset) {
+        for (int r = 0; r < h->nrep; ++r)
+            for (int k = MDPD_NUM_OBS; k <= 2 * MDPD_NUM_OBS; ++k) buf[(size_t)r * OBS_STRIDE + k] = 0.0;
+        CK(cudaMemcpy(h->obs_b, buf.data(), buf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return MDPD_OK;
+}
+
+int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params)
+{
+    if (!h || !params) return MDPD_ERR_INVALID_ARG;
+    if (!h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "not a batch handle");
+    for (int r = 0; r < h->nrep; ++r) {
+        std::string why;
+        int rc = validate_params(&params[r], why);
+        if (rc) return h->fail(rc, "replica " + std::to_string(r) + ": " + why);
+        const mdpd_params& o = h->rep_p[r];
+        for (int k = 0; k < 3; ++k)
+            if (params[r].box[k] != o.box[k] || params[r].box_lo[k] != o.box_lo[k] ||
+                params[r].periodic[k] != o.periodic[k])
+                return h->fail(MDPD_ERR_INVALID_ARG, "the box of a replica cannot change");
+        if (params[r].rc != o.rc || params[r].precision != o.precision || params[r].ntypes != o.ntypes)
+            return h->fail(MDPD_ERR_INVALID_ARG, "rc, precision and ntypes cannot change");
+    }
+    int rc = sync_check(h);
+    if (rc) return rc;
+    for (int r = 0; r < h->nrep; ++r) {
+        Rep& R = h->reps[r];
+        const uint32_t k0 = R.ph.key0, k1 = R.ph.key1;
+        Geo g{};
+        R.ph = Phys{};
+        make_geo_phys(params[r], 0, g, R.ph);
+        R.ph.key0 = k0;
+        R.ph.key1 = k1;
+        h->rep_p[r] = params[r];
+    }
+    // the records live in device memory: captured graphs stay valid
+    CK(cudaMemcpy(h->d_reps, h->reps.data(), sizeof(Rep) * (size_t)h->nrep, cudaMemcpyHostToDevice));
+    return MDPD_OK;
+}
+
 int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny, int32_t nz,
                    double voxel, const double origin[3], double wall_density,
                    double shell_thickness, int32_t wall_type, uint64_t seed)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "walls are not supported on a batch handle");
     if (h->walls_set) return h->fail(MDPD_ERR_INVALID_ARG, "walls already set");
     if (!solid || !origin || nx <= 0 || ny <= 0 || nz <= 0 || !(voxel > 0) || !is_fin(voxel))
         return h->fail(MDPD_ERR_INVALID_ARG, "bad mask dimensions or voxel size");
@@ -780,8 +1024,11 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return MDPD_OK;
-    launch_kick_drift(h->stream, (int)h->n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur),
-                      h->status);
+    if (h->nrep)
+        launch_kick_drift_batch(h->stream, h->cap, h->batch(), master(h, h->cur), h->status);
+    else
+        launch_kick_drift(h->stream, (int)h->n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur),
+                          h->status);
     h->prof_launches += 1;
     CK(cudaGetLastError());
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -879,7 +1126,12 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
         d_pos = h->fout;
         d_vel = h->x[1 - c];
     }
-    launch_load_state(st, n, h->cap, d_pos, d_vel, h->geo, master(h, c), h->type_by_id, h->status);
+    if (h->nrep)
+        launch_load_state_batch(st, h->cap, d_pos, d_vel, h->batch(), master(h, c), h->type_by_id,
+                                h->status);
+    else
+        launch_load_state(st, n, h->cap, d_pos, d_vel, h->geo, master(h, c), h->type_by_id,
+                          h->status);
     if ((rc = evaluate(h, nullptr, false))) return rc;
     return MDPD_OK;
 }
@@ -925,6 +1177,7 @@ int mdpd_forces_dev(mdpd_handle* h, double* force, double* rho) { return forces_
 int mdpd_observables(mdpd_handle* h, double out[MDPD_NUM_OBS])
 {
     if (!h || !out) return MDPD_ERR_INVALID_ARG;
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "batch handle: use mdpd_batch_observables");
     int rc = sync_check(h);
     if (rc) return rc;
     CK(cudaMemcpy(out, h->obs, MDPD_NUM_OBS * sizeof(double), cudaMemcpyDeviceToHost));
@@ -934,6 +1187,7 @@ int mdpd_observables(mdpd_handle* h, double out[MDPD_NUM_OBS])
 int mdpd_observables_mean(mdpd_handle* h, double out[MDPD_NUM_OBS], int32_t reset)
 {
     if (!h || !out) return MDPD_ERR_INVALID_ARG;
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "batch handle: use mdpd_batch_observables");
     int rc = sync_check(h);
     if (rc) return rc;
     double buf[MDPD_NUM_OBS + 1];
@@ -950,7 +1204,13 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs)
     int rc = sync_check(h);
     if (rc) return rc;
     double v = 0.0;
-    CK(cudaMemcpy(&v, h->obs + 2 * MDPD_NUM_OBS + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    if (h->nrep) {
+        std::vector<double> buf((size_t)h->nrep * OBS_STRIDE);
+        CK(cudaMemcpy(buf.data(), h->obs_b, buf.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int r = 0; r < h->nrep; ++r) v += buf[(size_t)r * OBS_STRIDE + 2 * MDPD_NUM_OBS + 1];
+    } else {
+        CK(cudaMemcpy(&v, h->obs + 2 * MDPD_NUM_OBS + 1, sizeof(double), cudaMemcpyDeviceToHost));
+    }
     *pairs = (int64_t)v;
     return MDPD_OK;
 }
@@ -966,6 +1226,8 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         if (value != MDPD_KERNELS_NLIST && value != MDPD_KERNELS_SCAN &&
             value != MDPD_KERNELS_NLIST_THREAD)
             return h->fail(MDPD_ERR_INVALID_ARG, "unknown kernel variant");
+        if (h->nrep && value == MDPD_KERNELS_SCAN)
+            return h->fail(MDPD_ERR_INVALID_ARG, "a batch runs the neighbour-list kernels only");
         CK(cudaStreamSynchronize(h->stream));
         h->kernels = (int)value;
         destroy_graphs(h);
@@ -986,6 +1248,7 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         return MDPD_OK;
     }
     case MDPD_OPT_WALL_DENSITY:
+        if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "a batch has no walls");
         CK(cudaStreamSynchronize(h->stream));
         h->want_phi = value != 0;
         destroy_graphs(h);
@@ -1023,6 +1286,7 @@ int mdpd_profile(mdpd_handle* h, double ms[MDPD_NUM_KCLASS], int64_t* steps, int
 int mdpd_set_params(mdpd_handle* h, const mdpd_params* p)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "batch handle: use mdpd_batch_set_params");
     std::string why;
     int rc = validate_params(p, why);
     if (rc) return h->fail(rc, why);
@@ -1069,6 +1333,7 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
     int rc = sync_check(h);
     if (rc) return rc;
     if (!abar) return h->fail(MDPD_ERR_INVALID_ARG, "abar is required");
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "the force VJP is not available on a batch handle");
     if ((rc = check_ptr_kind(h, abar, true)) || (rc = check_ptr_kind(h, xbar, true)) ||
         (rc = check_ptr_kind(h, ubar, true)) || (rc = check_ptr_kind(h, theta_bar, true)))
         return rc;
@@ -1181,6 +1446,11 @@ void mdpd_destroy(mdpd_handle* h)
     dfree(h->red_ticket);
     dfree(h->obs);
     dfree(h->mask_bits);
+    dfree(h->d_reps);
+    dfree(h->d_chunks);
+    dfree(h->d_cchunks);
+    dfree(h->d_wr);
+    dfree(h->obs_b);
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     for (auto e : h->prof_ev) cudaEventDestroy(e);

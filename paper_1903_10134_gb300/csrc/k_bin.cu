@@ -14,13 +14,30 @@ constexpr int BLOCK = 256;
 
 inline unsigned nblocks(int64_t n, int b = BLOCK) { return (unsigned)((n + b - 1) / b); }
 
-__global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Geo geo,
+// Batched kernels (BATCH = true) take their replica from the chunk of the
+// block (see Batch); single-system kernels index by the global thread id.
+template <bool BATCH>
+__global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Geo geo_p, Batch bt,
                             uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
                             uint32_t* __restrict__ count, uint32_t* __restrict__ status)
 {
     pdl_enter();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    int i;
+    bool valid;
+    int64_t cell0 = 0;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_GEO>(bt.reps, ch.x);
+        i = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = i < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
     int q[3];
     uint32_t st = 0;
 #pragma unroll
@@ -37,7 +54,7 @@ __global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Ge
         q[k] = c;
     }
     if (st) atomicOr(status, st);
-    const uint32_t c = (uint32_t)(q[0] + geo.nc[0] * (q[1] + geo.nc[1] * q[2]));
+    const uint32_t c = (uint32_t)(cell0 + q[0] + geo.nc[0] * (q[1] + geo.nc[1] * q[2]));
     cellof[i] = c;
     slot[i] = atomicAdd(&count[c], 1u);
 }
@@ -172,17 +189,33 @@ __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
     }
 }
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
                          const uint32_t* __restrict__ cellof, Master in, Master out,
-                         int gather_a, Geo geo, typename Vec4<T>::type* __restrict__ pos4,
+                         int gather_a, Geo geo_p, Batch bt, typename Vec4<T>::type* __restrict__ pos4,
                          typename Vec4<T>::type* __restrict__ vel4, uint32_t* __restrict__ cell_s)
 {
     pdl_enter();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    int s;
+    bool valid;
+    int64_t cell0 = 0;
+    uint32_t id0 = 0;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_GEO>(bt.reps, ch.x);
+        s = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+        id0 = rp->id0;
+    } else {
+        s = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = s < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
     const uint32_t i = src[s];
-    const uint32_t c = cellof[i];
+    const uint32_t c = cellof[i] - (uint32_t)cell0;      // cell within the replica
     const int q[3] = { (int)(c % (uint32_t)geo.nc[0]),
                        (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]),
                        (int)(c / ((uint32_t)geo.nc[0] * (uint32_t)geo.nc[1])) };
@@ -205,18 +238,32 @@ __global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
     for (int k = 0; k < 3; ++k)
         off[k] = (T)(xv[k] - geo.lo[k] - ((double)q[k] + 0.5) * geo.h[k]);
     pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
-    vel4[s] = make4((T)vv[0], (T)vv[1], (T)vv[2], pack_u32(T(0), pid));
+    // the random stream is keyed on ids within the replica
+    vel4[s] = make4((T)vv[0], (T)vv[1], (T)vv[2], pack_u32(T(0), pid - id0));
 }
 
 // Load a state given in id order (pos/vel interleaved xyz) into the master
 // arrays (index = id), wrapping periodic axes.
+template <bool BATCH>
 __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3,
-                             const double* __restrict__ vel3, Geo geo, Master m,
+                             const double* __restrict__ vel3, Geo geo_p, Batch bt, Master m,
                              const uint8_t* __restrict__ type_by_id, uint32_t* __restrict__ status)
 {
     pdl_enter();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    int i;
+    bool valid;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_GEO>(bt.reps, ch.x);
+        i = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+    } else {
+        i = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = i < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
     uint32_t st = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -273,7 +320,16 @@ void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, cons
                       uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_bin_count, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, x, geo, cellof, slot, count, status);
+    launch_pdl(k_bin_count<false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, x, geo, Batch{},
+               cellof, slot, count, status);
+}
+
+void launch_bin_count_batch(cudaStream_t st, int64_t cap, const double* x, const Batch& bt,
+                            uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
+{
+    if (bt.nchunk <= 0) return;
+    launch_pdl_smem(k_bin_count<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
+                    x, Geo{}, bt, cellof, slot, count, status);
 }
 
 int scan_num_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
@@ -308,11 +364,25 @@ void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uin
 {
     if (n <= 0) return;
     if (precision == 0)
-        launch_pdl(k_gather<double>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof, in, out, gather_a,
-                                                       geo, (D4*)pos4, (D4*)vel4, cell_s);
+        launch_pdl(k_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof,
+                   in, out, (int)gather_a, geo, Batch{}, (D4*)pos4, (D4*)vel4, cell_s);
     else
-        launch_pdl(k_gather<float>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof, in, out, gather_a,
-                                                      geo, (float4*)pos4, (float4*)vel4, cell_s);
+        launch_pdl(k_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof,
+                   in, out, (int)gather_a, geo, Batch{}, (float4*)pos4, (float4*)vel4, cell_s);
+}
+
+void launch_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* src,
+                         const uint32_t* cellof, const Master& in, const Master& out,
+                         bool gather_a, const Batch& bt, void* pos4, void* vel4, uint32_t* cell_s)
+{
+    if (bt.nchunk <= 0) return;
+    const dim3 g(bt.nchunk), b(BATCH_CHUNK);
+    if (precision == 0)
+        launch_pdl_smem(k_gather<double, true>, g, b, REP_SMEM, st, 0, cap, src, cellof, in, out,
+                        (int)gather_a, Geo{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
+    else
+        launch_pdl_smem(k_gather<float, true>, g, b, REP_SMEM, st, 0, cap, src, cellof, in, out,
+                        (int)gather_a, Geo{}, bt, (float4*)pos4, (float4*)vel4, cell_s);
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
@@ -320,7 +390,17 @@ void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
                        const uint8_t* type_by_id, uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_load_state, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, pos3, vel3, geo, m, type_by_id, status);
+    launch_pdl(k_load_state<false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, pos3, vel3, geo,
+               Batch{}, m, type_by_id, status);
+}
+
+void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, const double* vel3,
+                             const Batch& bt, const Master& m, const uint8_t* type_by_id,
+                             uint32_t* status)
+{
+    if (bt.nchunk <= 0) return;
+    launch_pdl_smem(k_load_state<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
+                    pos3, vel3, Geo{}, bt, m, type_by_id, status);
 }
 
 void launch_scatter_by_id(cudaStream_t st, int n, int64_t cap, const uint32_t* id,

@@ -30,25 +30,40 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 // evaluated under a branch: on the large porous systems this variant is picked
 // for, most warps have no candidate within r_d in an iteration, and a
 // branch-free weight (a reciprocal square root per candidate) measured slower.
-template <typename T>
+template <typename T, bool BATCH, bool WANT_PHI>
 __global__ void __launch_bounds__(PAIR_BLOCK, 12)
-k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
+k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
              const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
              const uint32_t* __restrict__ start, T* __restrict__ rho_out,
              uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
 {
     pdl_enter();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    int s;
+    bool valid;
+    int64_t cell0 = 0;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        s = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        s = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = s < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph = BATCH ? rp->ph : ph_p;
     const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
     const T inv_rd = (T)(1.0 / ph.rd);
     const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
     const auto pi = pos4[s];
     const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     const bool mobile = ph.list_all || mob_true;
-    // wall density of a mobile particle: sum over frozen partners within r_c of
-    // 15/(2 pi r_c^3) (1 - r/r_c)^2
-    const bool want_phi = ph.phi_out != nullptr && mob_true;
+    // wall density of a mobile particle (WANT_PHI): sum over frozen partners
+    // within r_c of 15/(2 pi r_c^3) (1 - r/r_c)^2
+    const bool want_phi = WANT_PHI && mob_true;
     const T inv_rc = (T)(1.0 / ph.rc);
     const T cphi = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rc * ph.rc * ph.rc));
     T phi = T(0);
@@ -69,7 +84,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
                 if (x < 0) continue;
                 const T sx = pi.x - (T)ox * (T)geo.h[0];
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
-                const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
+                const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
                 const uint32_t b = start[nc], e = start[nc + 1];
                 for (uint32_t j = b; j < e; ++j) {
                     const auto pj = pos4[j];
@@ -94,7 +109,7 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
     }
     rho_out[s] = acc;
     nl_count[s] = cnt;
-    if (ph.phi_out) ((T*)ph.phi_out)[s] = phi;
+    if (WANT_PHI) ((T*)ph.phi_out)[s] = phi;
 }
 
 // Warp-cooperative density pass: one warp per home cell.  The 27 neighbour
@@ -108,34 +123,49 @@ k_density_nl(int n, int64_t cap, Geo geo, Phys ph,
 constexpr int DC_WARPS = 4;
 constexpr int DC_GROUP = 8;
 
-template <typename T>
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(DC_WARPS * 32)
-k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
+k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                const typename Vec4<T>::type* __restrict__ pos4,
                const uint32_t* __restrict__ start, T* __restrict__ rho_out,
                uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
 {
     pdl_enter();
     using V = typename Vec4<T>::type;
+    static_assert(DC_WARPS == BATCH_CELL_CHUNK, "a cell chunk is one block");
     __shared__ V hpos[DC_WARPS][DC_GROUP];
     __shared__ uint32_t pre[DC_WARPS][28];
     __shared__ uint32_t cbase[DC_WARPS][27];
     __shared__ uint32_t ccnt[DC_WARPS][DC_GROUP];
     __shared__ uint32_t lst[DC_WARPS][NL_MAX][DC_GROUP];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t c = (int64_t)blockIdx.x * DC_WARPS + w;
-    if (c >= ncell) return;                       // whole warp
+    int64_t c, cell0 = 0;           // global cell, first cell of the replica
+    bool valid;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.cchunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        c = (int64_t)ch.y + w;
+        valid = w < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        c = (int64_t)blockIdx.x * DC_WARPS + w;
+        valid = c < ncell;
+    }
+    if (!valid) return;                           // whole warp
+    const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph = BATCH ? rp->ph : ph_p;
     const uint32_t hb = start[c], he = start[c + 1];
     if (hb == he) return;                         // whole warp
     int q0, q1, q2;
-    cell_coords((uint32_t)c, geo, q0, q1, q2);
+    cell_coords((uint32_t)(c - cell0), geo, q0, q1, q2);
     uint32_t cb = 0, cn = 0;
     if (lane < 27) {
         const int x = neighbour_index(q0, lane % 3 - 1, geo.nc[0], geo.periodic[0]);
         const int y = neighbour_index(q1, (lane / 3) % 3 - 1, geo.nc[1], geo.periodic[1]);
         const int z = neighbour_index(q2, lane / 9 - 1, geo.nc[2], geo.periodic[2]);
         if (x >= 0 && y >= 0 && z >= 0) {
-            const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
+            const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
             cb = start[nc];
             cn = start[nc + 1] - cb;
         }
@@ -239,9 +269,27 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo, Phys ph,
 // on the leading lanes (frozen wall particles need no force), then each of
 // those lanes walks its list with a two-stage software prefetch: list entries
 // two ahead, partner data one ahead.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(PAIR_BLOCK)
-k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
+// Minimum resident blocks per SM asked of the FP32 force kernel (0: the
+// compiler's default, kept for FP64).  The pair loop is latency-bound on its
+// partner gathers, so occupancy pays more than the few registers it costs: 8
+// blocks (64 registers, a 12-byte spill) measured 13 % faster than the
+// default 94 registers on the 4.4M-particle rock, and 8 beat 4 to 12 on a
+// batch (whose scalar constants sit in shared memory and take registers).
+#ifndef MDPD_FORCE_BATCH_MIN_BLOCKS
+#define MDPD_FORCE_BATCH_MIN_BLOCKS 8
+#endif
+#ifndef MDPD_FORCE_MIN_BLOCKS
+#define MDPD_FORCE_MIN_BLOCKS 8
+#endif
+template <typename T, bool BATCH>
+constexpr int force_min_blocks()
+{
+    return sizeof(T) != 4 ? 0 : (BATCH ? MDPD_FORCE_BATCH_MIN_BLOCKS : MDPD_FORCE_MIN_BLOCKS);
+}
+
+template <typename T, int MODE, bool BATCH>
+__global__ void __launch_bounds__(PAIR_BLOCK, (force_min_blocks<T, BATCH>()))
+k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
            const typename Vec4<T>::type* __restrict__ pos4,
            const typename Vec4<T>::type* __restrict__ vel4, const T* __restrict__ rho,
            const uint32_t* __restrict__ cell_s, const uint32_t* __restrict__ start,
@@ -255,7 +303,25 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     __shared__ T shift[27][3];
     __shared__ int act[PAIR_BLOCK];
     __shared__ int wsum[PAIR_BLOCK / 32];
-    load_tables(tab, ph);
+    int s0;
+    bool in_range;
+    int64_t cell0 = 0;
+    const Rep* rp = nullptr;
+    int rep_r = 0;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        rep_r = ch.x;
+        s0 = ch.y + (int)threadIdx.x;
+        in_range = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
+        in_range = s0 < n;
+    }
+    const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph = BATCH ? rp->ph : ph_p;      // in a batch: scalars only (see block_rep)
+    load_tables(tab, BATCH ? bt.reps[rep_r].ph : ph_p);
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
         shift[c][0] = (T)(c % 3 - 1) * (T)geo.h[0];
@@ -264,8 +330,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     }
     // compact the block's mobile particles onto the first lanes, in cell order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
-    const bool mob0 = s0 < n && ((ph.frozen >> m.type[s0]) & 1u) == 0u;
+    const bool mob0 = in_range && ((ph.frozen >> m.type[s0]) & 1u) == 0u;
     const unsigned bal = __ballot_sync(0xffffffffu, mob0);
     if (lane == 0) wsum[warp] = __popc(bal);
     __syncthreads();
@@ -276,7 +341,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         nact += wsum[w];
     }
     if (mob0) act[woff + __popc(bal & ((1u << lane) - 1u))] = s0;
-    if (MODE == FM_EVAL && s0 < n && !mob0) {
+    if (MODE == FM_EVAL && in_range && !mob0) {
 #pragma unroll
         for (int k = 0; k < 3; ++k) out[k * cap + s0] = 0.0;
     }
@@ -340,7 +405,7 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
                         const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
                         if (x < 0) continue;
                         const int code = image_code(ox, oy, oz);
-                        const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
+                        const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
                         const uint32_t b = start[nc], e = start[nc + 1];
                         for (uint32_t j = b; j < e; ++j) {
                             const V pj = pos4[j];
@@ -365,23 +430,24 @@ k_force_nl(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
-template <typename T>
+template <typename T, bool BATCH>
 void launch_force_nl_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const Geo& geo,
-                       const Phys& ph, const MaskDev& mk, const void* pos4, const void* vel4,
-                       const void* rho, const uint32_t* cell_s, const uint32_t* start,
-                       const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,
-                       int step_offset, const Master& m, double* out, double* partials,
-                       uint32_t* status)
+                       const Phys& ph, const Batch& bt, const MaskDev& mk, const void* pos4,
+                       const void* vel4, const void* rho, const uint32_t* cell_s,
+                       const uint32_t* start, const uint32_t* nl, const uint32_t* nl_count,
+                       const uint64_t* step_ptr, int step_offset, const Master& m, double* out,
+                       double* partials, uint32_t* status)
 {
     using V = typename Vec4<T>::type;
-    const int nb = force_num_blocks(n);
+    const int nb = BATCH ? bt.nchunk : force_num_blocks(n);
+    const size_t smem = BATCH ? REP_SMEM : 0;
     const V* p = (const V*)pos4;
     const V* v = (const V*)vel4;
     const T* r = (const T*)rho;
 #define MDPD_FNL(MODE_)                                                                    \
-    launch_pdl(k_force_nl<T, MODE_>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, mk, p, v, r, cell_s, \
-                                                    start, nl, nl_count, step_ptr,        \
-                                                    step_offset, m, out, partials, status)
+    launch_pdl_smem(k_force_nl<T, MODE_, BATCH>, dim3(nb), dim3(PAIR_BLOCK), smem, st, n, cap, \
+                    geo, ph, bt, mk, p, v, r, cell_s, start, nl, nl_count, step_ptr,       \
+                    step_offset, m, out, partials, status)
     if (mode == FM_EVAL) MDPD_FNL(FM_EVAL);
     else if (mode == FM_LAST) MDPD_FNL(FM_LAST);
     else MDPD_FNL(FM_FUSED);
@@ -396,12 +462,29 @@ void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const
 {
     if (n <= 0) return;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
+    const bool phi = ph.phi_out != nullptr;
     if (precision == 0)
-        launch_pdl(k_density_nl<double>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, (const D4*)pos4, cell_s,
-                                                        start, (double*)rho, nl, nl_count);
+        launch_pdl(phi ? k_density_nl<double, false, true> : k_density_nl<double, false, false>,
+                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const D4*)pos4,
+                   cell_s, start, (double*)rho, nl, nl_count);
     else
-        launch_pdl(k_density_nl<float>, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, (const float4*)pos4,
-                                                       cell_s, start, (float*)rho, nl, nl_count);
+        launch_pdl(phi ? k_density_nl<float, false, true> : k_density_nl<float, false, false>,
+                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const float4*)pos4,
+                   cell_s, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                             const void* pos4, const uint32_t* cell_s, const uint32_t* start,
+                             void* rho, uint32_t* nl, uint32_t* nl_count)
+{
+    if (bt.nchunk <= 0) return;
+    const dim3 g(bt.nchunk), b(PAIR_BLOCK);
+    if (precision == 0)
+        launch_pdl_smem(k_density_nl<double, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const D4*)pos4, cell_s, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl_smem(k_density_nl<float, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const float4*)pos4, cell_s, start, (float*)rho, nl, nl_count);
 }
 
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
@@ -411,12 +494,25 @@ void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t 
     if (ncell <= 0) return;
     const unsigned nb = (unsigned)((ncell + DC_WARPS - 1) / DC_WARPS);
     if (precision == 0)
-        launch_pdl(k_density_cell<double>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap, geo, ph, (const D4*)pos4,
-                                                             start, (double*)rho, nl, nl_count);
+        launch_pdl(k_density_cell<double, false>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap,
+                   geo, ph, Batch{}, (const D4*)pos4, start, (double*)rho, nl, nl_count);
     else
-        launch_pdl(k_density_cell<float>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap, geo, ph,
-                                                            (const float4*)pos4, start,
-                                                            (float*)rho, nl, nl_count);
+        launch_pdl(k_density_cell<float, false>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap,
+                   geo, ph, Batch{}, (const float4*)pos4, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_cell_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                               const void* pos4, const uint32_t* start, void* rho, uint32_t* nl,
+                               uint32_t* nl_count)
+{
+    if (bt.ncchunk <= 0) return;
+    const dim3 g(bt.ncchunk), b(DC_WARPS * 32);
+    if (precision == 0)
+        launch_pdl_smem(k_density_cell<double, true>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const D4*)pos4, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl_smem(k_density_cell<float, true>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const float4*)pos4, start, (float*)rho, nl, nl_count);
 }
 
 void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
@@ -427,11 +523,31 @@ void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int6
                      double* partials, uint32_t* status)
 {
     if (precision == 0)
-        launch_force_nl_t<double>(st, mode, n, cap, geo, ph, mk, pos4, vel4, rho, cell_s, start,
-                                  nl, nl_count, step_ptr, step_offset, m, out, partials, status);
+        launch_force_nl_t<double, false>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
+                                         cell_s, start, nl, nl_count, step_ptr, step_offset, m,
+                                         out, partials, status);
     else
-        launch_force_nl_t<float>(st, mode, n, cap, geo, ph, mk, pos4, vel4, rho, cell_s, start,
-                                 nl, nl_count, step_ptr, step_offset, m, out, partials, status);
+        launch_force_nl_t<float, false>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
+                                        cell_s, start, nl, nl_count, step_ptr, step_offset, m,
+                                        out, partials, status);
+}
+
+void launch_force_nl_batch(cudaStream_t st, int precision, ForceMode mode, int64_t cap,
+                           const Batch& bt, const void* pos4, const void* vel4, const void* rho,
+                           const uint32_t* cell_s, const uint32_t* start, const uint32_t* nl,
+                           const uint32_t* nl_count, const uint64_t* step_ptr, int step_offset,
+                           const Master& m, double* out, double* partials, uint32_t* status)
+{
+    const MaskDev none{};
+    if (bt.nchunk <= 0) return;
+    if (precision == 0)
+        launch_force_nl_t<double, true>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
+                                        cell_s, start, nl, nl_count, step_ptr, step_offset, m,
+                                        out, partials, status);
+    else
+        launch_force_nl_t<float, true>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
+                                       cell_s, start, nl, nl_count, step_ptr, step_offset, m,
+                                       out, partials, status);
 }
 
 }  // namespace mdpd

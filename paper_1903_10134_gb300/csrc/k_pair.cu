@@ -143,12 +143,26 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
-__global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, Master m,
-                             uint32_t* __restrict__ status)
+template <bool BATCH>
+__global__ void k_kick_drift(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
+                             Master m, uint32_t* __restrict__ status)
 {
     pdl_enter();
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    int s;
+    bool valid;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        s = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+    } else {
+        s = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = s < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph = BATCH ? rp->ph : ph_p;
     if ((ph.frozen >> m.type[s]) & 1u) return;
     double x[3], v[3];
 #pragma unroll
@@ -177,6 +191,30 @@ __global__ void k_kick_drift(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk, M
 // Every addition happens in a fixed order, so the result is reproducible.
 constexpr int RED_CHUNK = 256;
 constexpr int RED_THREADS = RED_CHUNK;
+
+// Observables from the summed partials t (momentum 3, sum v^2 3, virial 6,
+// mobile count, pairs): o = momentum, kinetic energy, kT, virial, sum v^2,
+// mobile count, step; obs[2 * MDPD_NUM_OBS + 1] = the directed pair count.
+__device__ void finish_obs(const double (&t)[NOBS], uint64_t step, double* __restrict__ obs,
+                           double* __restrict__ obs_sum, double* __restrict__ obs_count,
+                           int advance)
+{
+    double o[MDPD_NUM_OBS];
+    for (int k = 0; k < 3; ++k) o[k] = t[k];
+    o[3] = 0.5 * (t[3] + t[4] + t[5]);
+    const double nm = t[12];
+    o[4] = nm > 1.0 ? 2.0 * o[3] / (3.0 * (nm - 1.0)) : 0.0;
+    for (int k = 0; k < 6; ++k) o[5 + k] = t[6 + k];
+    for (int k = 0; k < 3; ++k) o[11 + k] = t[3 + k];
+    o[14] = nm;
+    o[15] = (double)step;
+    for (int k = 0; k < MDPD_NUM_OBS; ++k) obs[k] = o[k];
+    obs[2 * MDPD_NUM_OBS + 1] = t[13];     // directed pairs with r < r_c
+    if (advance) {
+        for (int k = 0; k < MDPD_NUM_OBS; ++k) obs_sum[k] += o[k];
+        *obs_count += 1.0;
+    }
+}
 
 __global__ void __launch_bounds__(RED_THREADS)
 k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict__ l1,
@@ -223,23 +261,59 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
         double t[NOBS];
         for (int k = 0; k < NOBS; ++k) t[k] = s16[k][16];
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
-        double o[MDPD_NUM_OBS];
-        for (int k = 0; k < 3; ++k) o[k] = t[k];
-        o[3] = 0.5 * (t[3] + t[4] + t[5]);
-        const double nm = t[12];
-        o[4] = nm > 1.0 ? 2.0 * o[3] / (3.0 * (nm - 1.0)) : 0.0;
-        for (int k = 0; k < 6; ++k) o[5 + k] = t[6 + k];
-        for (int k = 0; k < 3; ++k) o[11 + k] = t[3 + k];
-        o[14] = nm;
-        o[15] = (double)step;
-        for (int k = 0; k < MDPD_NUM_OBS; ++k) obs[k] = o[k];
-        obs[2 * MDPD_NUM_OBS + 1] = t[13];     // directed pairs with r < r_c
-        if (advance) {
-            for (int k = 0; k < MDPD_NUM_OBS; ++k) obs_sum[k] += o[k];
-            *obs_count += 1.0;
-            *step_ptr = step;
-        }
+        finish_obs(t, step, obs, obs_sum, obs_count, advance);
+        if (advance) *step_ptr = step;
         *ticket = 0u;
+    }
+}
+
+// Per-replica reduction of a batch: block r adds the per-warp partials of
+// replica r's chunks, [wr[r].x, wr[r].y), in a fixed order (a strided sum per
+// thread, then 16 partial sums per observable, then one), and writes the
+// replica's observables to obs[r * OBS_STRIDE ...] (current values, running
+// sums, count, pairs: the layout of a single system).  The block holding the
+// last ticket advances the shared step counter.
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce_obs_batch(const double* __restrict__ partials, int nparts, const int2* __restrict__ wr,
+                   unsigned* __restrict__ ticket, double* __restrict__ obs,
+                   uint64_t* __restrict__ step_ptr, int advance)
+{
+    pdl_enter();
+    __shared__ double sh[NOBS][RED_THREADS + 1];
+    __shared__ double s16[NOBS][17];
+    const int2 w = wr[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < NOBS; ++k) {
+        double v = 0.0;
+        for (int q = w.x + (int)threadIdx.x; q < w.y; q += RED_THREADS)
+            v += partials[(int64_t)k * nparts + q];
+        sh[k][threadIdx.x] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NOBS * 16) {
+        const int k = threadIdx.x >> 4, part = threadIdx.x & 15;
+        double v = 0.0;
+#pragma unroll
+        for (int l = 0; l < RED_THREADS / 16; ++l) v += sh[k][part * (RED_THREADS / 16) + l];
+        s16[k][part] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[NOBS];
+        for (int k = 0; k < NOBS; ++k) {
+            double v = 0.0;
+            for (int l = 0; l < 16; ++l) v += s16[k][l];
+            t[k] = v;
+        }
+        const uint64_t step = *step_ptr + (advance ? 1u : 0u);
+        double* o = obs + (int64_t)blockIdx.x * OBS_STRIDE;
+        finish_obs(t, step, o, o + MDPD_NUM_OBS, o + 2 * MDPD_NUM_OBS, advance);
+        __threadfence();
+        const bool last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        if (last) {
+            if (advance) *step_ptr = step;
+            *ticket = 0u;
+        }
     }
 }
 
@@ -311,7 +385,25 @@ void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, cons
                        const MaskDev& mk, const Master& m, uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_kick_drift, dim3((n + 255) / 256), dim3(256), st, n, cap, geo, ph, mk, m, status);
+    launch_pdl(k_kick_drift<false>, dim3((n + 255) / 256), dim3(256), st, n, cap, geo, ph, Batch{},
+               mk, m, status);
+}
+
+void launch_kick_drift_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
+                             uint32_t* status)
+{
+    if (bt.nchunk <= 0) return;
+    launch_pdl_smem(k_kick_drift<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
+                    Geo{}, Phys{}, bt, MaskDev{}, m, status);
+}
+
+void launch_reduce_obs_batch(cudaStream_t st, const double* partials, int nparts, const int2* wr,
+                             int nrep, unsigned* ticket, double* obs, uint64_t* step_ptr,
+                             int advance)
+{
+    if (nrep <= 0) return;
+    launch_pdl(k_reduce_obs_batch, dim3(nrep), dim3(RED_THREADS), st, partials, nparts, wr, ticket,
+               obs, step_ptr, advance);
 }
 
 int reduce_l1_blocks(int nparts) { return (nparts + RED_CHUNK - 1) / RED_CHUNK; }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstddef>
 #include <utility>
 
 #include "mdpd.h"
@@ -39,6 +40,34 @@ struct Phys {
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
     double A[64], B[64], gamma[64], sigma[64];
 };
+
+// One member of a batch of independent systems: its box and cell lattice,
+// the global index of its first cell and of its first particle, and its
+// physical constants.  Kernels of a batch map each block to one chunk of one
+// replica and copy the replica's record to shared memory.
+struct alignas(16) Rep {
+    Geo geo;
+    int64_t cell0;      // first cell of the replica in the concatenated lattice
+    uint32_t id0;       // first particle id (= first slot) of the replica
+    uint32_t n;         // particles of the replica
+    alignas(16) Phys ph;
+};
+static_assert(offsetof(Rep, ph) % 16 == 0 && sizeof(Rep) % 16 == 0, "Rep is copied in 16-byte words");
+
+// Kernel-side view of a batch.  Particles of replica r always occupy the
+// slots [reps[r].id0, reps[r].id0 + reps[r].n), in every ordering, so the
+// work can be cut into chunks that never straddle two replicas:
+//   chunks[b]  = (replica, first slot, count <= 128, 0)   for particle kernels
+//   cchunks[b] = (replica, first cell, count <= 4, 0)     for cell kernels
+struct Batch {
+    const Rep* reps;
+    const int4* chunks;
+    const int4* cchunks;
+    int nchunk, ncchunk;
+};
+
+constexpr int BATCH_CHUNK = 128;       // particles per chunk
+constexpr int BATCH_CELL_CHUNK = 4;    // cells per chunk (warps of the cell kernel)
 
 // Solid-voxel reflection mask (1 bit per voxel, x fastest); bits == nullptr
 // means no mask.
@@ -80,13 +109,13 @@ __device__ __forceinline__ void pdl_enter()
 }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
-                              Args&&... args)
+inline cudaError_t launch_pdl_smem(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                   cudaStream_t st, Args&&... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = block;
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -94,6 +123,35 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cud
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t st,
+                              Args&&... args)
+{
+    return launch_pdl_smem(kern, grid, block, 0, st, std::forward<Args>(args)...);
+}
+
+// The replica record of this block's chunk, copied in part to dynamic shared
+// memory (the launch provides REP_SMEM bytes): REP_GEO copies the geometry
+// (everything before ph), REP_SCALARS also the scalar constants of ph (not the
+// per-type-pair tables, which a kernel that needs them reads from reps[r]).
+enum RepPart { REP_GEO = 0, REP_SCALARS = 1 };
+__host__ __device__ constexpr size_t rep_part_bytes(int part)
+{
+    return ((part == REP_GEO ? offsetof(Rep, ph) : offsetof(Rep, ph) + offsetof(Phys, A)) + 15) / 16 * 16;
+}
+constexpr size_t REP_SMEM = rep_part_bytes(REP_SCALARS);
+
+template <int PART>
+__device__ __forceinline__ const Rep& block_rep(const Rep* __restrict__ reps, int r)
+{
+    extern __shared__ uint4 rep_smem[];
+    constexpr int words = (int)(rep_part_bytes(PART) / sizeof(uint4));
+    const uint4* src = reinterpret_cast<const uint4*>(reps + r);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) rep_smem[k] = src[k];
+    __syncthreads();
+    return *reinterpret_cast<const Rep*>(rep_smem);
 }
 
 constexpr int OBS_PARTIALS = 16;   // observable slots per partial (14 used)
@@ -150,6 +208,35 @@ int reduce_l1_blocks(int nparts);
 void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
                        unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
                        uint64_t* step_ptr, int advance);
+
+// ---- launchers (batch of replicas; see Batch) ------------------------------
+constexpr int OBS_STRIDE = 2 * MDPD_NUM_OBS + 2;   // per-replica observable record
+void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, const double* vel3,
+                             const Batch& bt, const Master& m, const uint8_t* type_by_id,
+                             uint32_t* status);
+void launch_bin_count_batch(cudaStream_t st, int64_t cap, const double* x, const Batch& bt,
+                            uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status);
+void launch_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* src,
+                         const uint32_t* cellof, const Master& in, const Master& out,
+                         bool gather_a, const Batch& bt, void* pos4, void* vel4, uint32_t* cell_s);
+void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                             const void* pos4, const uint32_t* cell_s, const uint32_t* start,
+                             void* rho, uint32_t* nl, uint32_t* nl_count);
+void launch_density_cell_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                               const void* pos4, const uint32_t* start, void* rho, uint32_t* nl,
+                               uint32_t* nl_count);
+// Partials: 4 per chunk (bt.nchunk * 4 in all).
+void launch_force_nl_batch(cudaStream_t st, int precision, ForceMode mode, int64_t cap,
+                           const Batch& bt, const void* pos4, const void* vel4, const void* rho,
+                           const uint32_t* cell_s, const uint32_t* start, const uint32_t* nl,
+                           const uint32_t* nl_count, const uint64_t* step_ptr, int step_offset,
+                           const Master& m, double* out, double* partials, uint32_t* status);
+void launch_kick_drift_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
+                             uint32_t* status);
+// wr[r] = the range of partials of replica r; obs holds nrep * OBS_STRIDE doubles.
+void launch_reduce_obs_batch(cudaStream_t st, const double* partials, int nparts, const int2* wr,
+                             int nrep, unsigned* ticket, double* obs, uint64_t* step_ptr,
+                             int advance);
 
 // ---- launchers (adjoint) ---------------------------------------------------
 // VJP of one force evaluation at the current cell-ordered state (lists built

@@ -297,3 +297,29 @@ def contact_slit(A_sl: float, seed: int = 1, precision: int = 1, steps: int = 14
     return Workload("contact_slit", p, pos, vel, np.zeros(4000, np.int32), seed, mask=mask,
                     voxel=voxel, origin=lo, wall_density=35.0 / 6.0, shell=1.0, wall_type=1,
                     wall_seed=seed + 1000, steps=steps)
+
+
+def batch_slabs(nrep: int = 256, n_range=(2000, 20000), A_range=(-50.0, -30.0),
+                B_range=(15.0, 35.0), seed: int = 1, precision: int = 1,
+                steps: int = 50, density: float = 6.0) -> list:
+    """Many small liquid slabs of uneven size and parameters, advanced together
+    as one batch (ensembles or A, B sweeps and fits).  Replica r: N_r drawn
+    uniformly from n_range, A_r and B_r uniformly from their ranges, a periodic
+    box 3 L x L x L with L = (N_r / density)^(1/3) holding a liquid block of
+    density `density` over its middle third in x (random positions), Maxwell
+    velocities at kT = 1, seed `seed` + r.  `steps` is the length of one
+    window."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(nrep):
+        n_r = int(rng.integers(n_range[0], n_range[1] + 1))
+        A = float(rng.uniform(*A_range))
+        B = float(rng.uniform(*B_range))
+        L = (n_r / density) ** (1.0 / 3.0)
+        p = MDPDParams(box=(3 * L, L, L), precision=precision)
+        p.set_pair(0, 0, A=A, B=B)
+        pos = uniform_positions(n_r, (L, 0.0, 0.0), (2 * L, L, L), rng)
+        vel = maxwell_velocities(n_r, p.kT, rng)
+        out.append(Workload("batch_slab", p, pos, vel, np.zeros(n_r, np.int32), seed + r,
+                            steps=steps))
+    return out

@@ -95,7 +95,8 @@ SYMBOLS = (
     "mdpd_profile",
     "mdpd_describe", "mdpd_autotune", "mdpd_set_params", "mdpd_set_step",
     "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
-    "mdpd_last_error",
+    "mdpd_last_error", "mdpd_create_batch", "mdpd_num_replicas", "mdpd_batch_observables",
+    "mdpd_batch_set_params",
 )
 
 
@@ -139,6 +140,10 @@ def lib(build_if_stale: bool = True):
     L.mdpd_set_step.argtypes = [P, i64]
     L.mdpd_get_accel_dev.argtypes = [P, P]
     L.mdpd_force_vjp_dev.argtypes = [P, P, P, P, P]
+    L.mdpd_create_batch.argtypes = [i32, P, P, P, P, P, P, P, C.POINTER(P)]
+    L.mdpd_num_replicas.argtypes = [P, C.POINTER(i32)]
+    L.mdpd_batch_observables.argtypes = [P, P, i32, i32]
+    L.mdpd_batch_set_params.argtypes = [P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -204,6 +209,40 @@ def mdpd_create_dev(params, pos_t, vel_t, type_t, seed: int, stream=None):
     _check(lib().mdpd_create_dev(C.byref(cp), n, _tptr(pos_t), _tptr(vel_t), _tptr(type_t),
                                  int(seed), _stream_ptr(stream), C.byref(h)))
     return h
+
+
+def mdpd_create_batch(params_list, n_list, pos, vel, type, seeds, stream=None):
+    """params_list[r], n_list[r], seeds[r] per replica; pos/vel (N, 3), type (N,)
+    with replica 0's particles first."""
+    nrep = len(params_list)
+    ns = _arr([int(v) for v in n_list], np.int64, (nrep,))
+    N = int(ns.sum())
+    pos = _arr(pos, np.float64, (N, 3))
+    vel = _arr(vel, np.float64, (N, 3))
+    typ = _arr(type, np.int32, (N,))
+    cps = (Params * nrep)(*[to_c_params(p) for p in params_list])
+    sd = _arr([int(v) for v in seeds], np.uint64, (nrep,))
+    h = C.c_void_p()
+    _check(lib().mdpd_create_batch(nrep, cps, _p(ns), _p(pos), _p(vel), _p(typ), _p(sd),
+                                   _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def mdpd_num_replicas(h) -> int:
+    r = C.c_int32()
+    _check(lib().mdpd_num_replicas(h, C.byref(r)), h)
+    return int(r.value)
+
+
+def mdpd_batch_observables(h, mean: bool = False, reset: bool = False) -> np.ndarray:
+    out = np.zeros((mdpd_num_replicas(h), NUM_OBS))
+    _check(lib().mdpd_batch_observables(h, _p(out), int(mean), int(reset)), h)
+    return out
+
+
+def mdpd_batch_set_params(h, params_list):
+    cps = (Params * len(params_list))(*[to_c_params(p) for p in params_list])
+    _check(lib().mdpd_batch_set_params(h, cps), h)
 
 
 def mdpd_set_walls(h, solid, voxel: float, origin, wall_density: float, shell_thickness: float,
@@ -370,6 +409,86 @@ def mdpd_destroy(h):
 def mdpd_last_error(h=None) -> str:
     msg = lib().mdpd_last_error(h)
     return msg.decode() if msg else ""
+
+
+class Batch:
+    """Owning wrapper of a batch handle: nrep independent systems advanced by
+    one launch per kernel (see ``mdpd_create_batch``)."""
+
+    def __init__(self, params_list, n_list, pos, vel, type, seeds, stream=None):
+        self.h = mdpd_create_batch(params_list, n_list, pos, vel, type, seeds, stream)
+        self.n_list = [int(v) for v in n_list]
+        self.offsets = np.concatenate([[0], np.cumsum(self.n_list)]).astype(int)
+
+    @classmethod
+    def from_workloads(cls, ws, stream=None, precision=None):
+        ps = [w.params if precision is None else w.params.copy(precision=precision) for w in ws]
+        return cls(ps, [w.n for w in ws], np.concatenate([w.pos for w in ws]),
+                   np.concatenate([w.vel for w in ws]), np.concatenate([w.type for w in ws]),
+                   [w.seed for w in ws], stream)
+
+    @property
+    def nrep(self) -> int:
+        return len(self.n_list)
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+    def step(self, nsteps: int):
+        mdpd_step(self.h, nsteps)
+
+    def sync(self):
+        mdpd_sync(self.h)
+
+    def state(self):
+        return mdpd_get_state(self.h)
+
+    def replica_state(self, r: int):
+        x, v, t, rho = self.state()
+        a, b = self.offsets[r], self.offsets[r + 1]
+        return x[a:b], v[a:b], t[a:b], rho[a:b]
+
+    def set_state(self, pos, vel):
+        mdpd_set_state(self.h, pos, vel)
+
+    def forces(self):
+        return mdpd_forces(self.h)
+
+    def observables(self, mean: bool = False, reset: bool = False):
+        return mdpd_batch_observables(self.h, mean, reset)
+
+    def set_params(self, params_list):
+        mdpd_batch_set_params(self.h, params_list)
+
+    def pair_count(self):
+        return mdpd_pair_count(self.h)
+
+    def set_option(self, option, value):
+        mdpd_set_option(self.h, option, value)
+
+    def profile(self):
+        return mdpd_profile(self.h)
+
+    def autotune(self, reps: int = 5):
+        return mdpd_autotune(self.h, reps)
+
+    def close(self):
+        if getattr(self, "h", None):
+            mdpd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class System:
