@@ -53,7 +53,7 @@ DESC = {
 }
 
 
-def make_workload(name: str, precision: int, seed: int, nvox: int = 256):
+def make_workload(name: str, precision: int, seed: int, nvox: int = 256, nrep: int = 256):
     from paper_1903_10134_gb300 import inputs as I
     if name == "bulk":
         return I.bulk(seed=seed, precision=precision)
@@ -64,7 +64,7 @@ def make_workload(name: str, precision: int, seed: int, nvox: int = 256):
     if name == "rock":
         return I.rock(nvox=nvox, seed=seed, precision=precision)
     if name == "batch":
-        return I.batch_slabs(nrep=256, seed=seed, precision=precision)
+        return I.batch_slabs(nrep=nrep, seed=seed, precision=precision)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -214,7 +214,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import oracle as O
-    w = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
+    w = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
     if args.workload == "batch":
         info = oracle_throughput_batch(w, args.ref_seconds)
         value = info["value"]
@@ -304,7 +304,8 @@ def run_ours(args):
 
     dev = torch.cuda.current_device()
     prec = 0 if args.precision == "fp64" else 1
-    w = make_workload(args.workload, prec, seed=replica_seed(rank), nvox=args.nvox)
+    w = make_workload(args.workload, prec, seed=replica_seed(rank), nvox=args.nvox,
+                      nrep=args.nrep)
     stream = torch.cuda.Stream()
     if args.workload == "batch":
         s = mdpd.Batch.from_workloads(w, stream=stream)
@@ -312,9 +313,12 @@ def run_ours(args):
         s = mdpd.System.from_workload(w, stream=stream)
     tuned = None
     if args.kernels == "auto":
-        chosen, tms = s.autotune()
+        res = s.autotune()
+        chosen, tms = res
         tuned = {"chosen": {mdpd.KERNELS_NLIST: "nlist", mdpd.KERNELS_NLIST_THREAD: "nlist-thread"}[chosen],
-                 "density_ms": {"nlist": tms[0], "nlist-thread": tms[1]}}
+                 "density_ms": {"nlist": tms[0], "nlist-thread": tms[1]},
+                 "force_lanes": res.lanes,
+                 "force_ms": {str(l): t for l, t in zip((1, 2, 4), res.force_ms) if t >= 0}}
     elif args.kernels != "nlist":
         s.set_option(mdpd.OPT_KERNELS, {"scan": mdpd.KERNELS_SCAN,
                                         "nlist-thread": mdpd.KERNELS_NLIST_THREAD}[args.kernels])
@@ -408,7 +412,7 @@ def run_ours(args):
         traffic = force_traffic(args.workload, args.precision)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
-            wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox)
+            wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
             if args.workload == "batch":
                 info = oracle_throughput_batch(wc, args.cpu_seconds)
                 sample = (f"one FP64 oracle step of each of the first {info['replicas']} of "
@@ -466,6 +470,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
+    ap.add_argument("--nrep", type=int, default=256, help="replicas of the batch workload")
     ap.add_argument("--kernels", choices=("auto", "nlist", "nlist-thread", "scan"), default="auto")
     ap.add_argument("--profile-every", type=int, default=10,
                     help="record per-kernel events on every k-th timed step")

@@ -227,12 +227,18 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *                      Algorithm 1 step 2; read with mdpd_get_wall_density);
  *                      the thread-per-particle density variant is used while
  *                      it is on.  0 (default): off.
+ *   MDPD_OPT_FORCE_LANES  1, 2 or 4 (default 1): lanes that share one
+ *                      particle's partner list in the force pass (more warps
+ *                      for small systems; the partner sums are combined in a
+ *                      fixed order, so results are reproducible for a given
+ *                      setting but round differently from another setting).
+ *                      A batch handle accepts 1 only.
  *   MDPD_OPT_PROFILE_EVERY  m >= 1: with MDPD_OPT_PROFILE on, record the events
  *                      on every m-th step only (default 1), which keeps their
  *                      cost out of most steps.
  */
 enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3,
-       MDPD_OPT_PROFILE_EVERY = 4, MDPD_OPT_WALL_DENSITY = 5 };
+       MDPD_OPT_PROFILE_EVERY = 4, MDPD_OPT_WALL_DENSITY = 5, MDPD_OPT_FORCE_LANES = 6 };
 enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1, MDPD_KERNELS_NLIST_THREAD = 2 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
@@ -284,9 +290,13 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
                        double* theta_bar);
 
 /* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD)
- * on the current state, reps launches each, and keep the faster one.  The
- * trajectory is not advanced.  chosen (may be NULL) receives the variant, ms
- * (may be NULL, 2 doubles) the mean time of each.  Synchronises. */
+ * and then the force pass at 1, 2 and 4 lanes per particle
+ * (MDPD_OPT_FORCE_LANES; 1 only on a batch) on the current state, reps
+ * launches each, and keep the fastest of each.  The trajectory is not
+ * advanced.  chosen (may be NULL, 2 ints) receives the density variant and
+ * the lanes per particle; ms (may be NULL, 5 doubles) the mean time of each
+ * density variant, then of the force pass at 1, 2, 4 lanes (-1: not tried).
+ * Synchronises. */
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms);
 
 /* Grid of the cell lattice (cells per axis) and the kernel launches one step

@@ -74,13 +74,14 @@ struct mdpd_handle {
     void* phi = nullptr;             // cap wall densities (cell order)
     bool want_phi = false;
     int kernels = MDPD_KERNELS_NLIST;
+    int force_lpp = 1;               // lanes per particle of the force pass (single system)
     bool walls_set = false;
     std::vector<int32_t> h_type;
     int64_t steps_host = 0;
 
-    // graphs[profiled][mode: 0 fused, 1 last][cur]
+    // graphs[profiled][mode: 0 fused, 1 last][cur][first half-kick in the binning]
     bool use_graph = true;
-    Graphs g[2][2][2];
+    Graphs g[2][2][2][2];
     cudaEvent_t tev[EV_PER_STEP] = {};
 
     // profiling ring
@@ -210,9 +211,9 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->slot, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->key, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->src, c * sizeof(uint32_t));
-    const size_t nparts = std::max((size_t)obs_num_partials((int)c), (size_t)h->nchunk * (PAIR_BLOCK_WARPS));
+    const size_t nparts = std::max((size_t)obs_num_partials((int)c, 4), (size_t)h->nchunk * (PAIR_BLOCK_WARPS));
     if (!rc) rc = dalloc(h, &h->partials, nparts * OBS_PARTIALS * sizeof(double));
-    if (!rc) rc = dalloc(h, &h->red_l1, (size_t)(reduce_l1_blocks(obs_num_partials((int)c)) + 1) * OBS_PARTIALS * sizeof(double));
+    if (!rc) rc = dalloc(h, &h->red_l1, (size_t)(reduce_l1_blocks(obs_num_partials((int)c, 4)) + 1) * OBS_PARTIALS * sizeof(double));
     if (!rc) rc = dalloc(h, &h->fout, 3 * c * sizeof(double));
     if (!rc) rc = dalloc(h, &h->type_by_id, c);
     if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
@@ -254,11 +255,12 @@ void destroy_graphs(mdpd_handle* h)
 {
     for (auto& a : h->g)
         for (auto& b : a)
-            for (auto& gg : b) {
-                if (gg.exec) cudaGraphExecDestroy(gg.exec);
-                if (gg.graph) cudaGraphDestroy(gg.graph);
-                gg = Graphs();
-            }
+            for (auto& c : b)
+                for (auto& gg : c) {
+                    if (gg.exec) cudaGraphExecDestroy(gg.exec);
+                    if (gg.graph) cudaGraphDestroy(gg.graph);
+                    gg = Graphs();
+                }
 }
 
 bool is_fin(double x) { return std::isfinite(x); }
@@ -326,6 +328,7 @@ void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
     f.ntypes = p.ntypes;
     f.xi_dist = p.xi_dist;
     f.rho_self = p.rho_self ? 1 : 0;
+    f.prec32 = p.precision == 1 ? 1 : 0;
     f.key0 = (uint32_t)seed;
     f.key1 = (uint32_t)(seed >> 32);
     for (int a = 0; a < 8; ++a)
@@ -335,6 +338,7 @@ void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
             f.gamma[a * 8 + b] = p.gamma[a][b];
             f.sigma[a * 8 + b] = std::sqrt(2.0 * p.gamma[a][b] * p.kT);
         }
+    fill_derived(f, g);
 }
 
 void setup_geo_phys(mdpd_handle* h)
@@ -382,29 +386,37 @@ void record(mdpd_handle* h, cudaEvent_t* evs, int k)
     if (evs) cudaEventRecordWithFlags(evs[k], h->stream, cudaEventRecordExternal);
 }
 
-// Bin: count, scan, scatter, per-cell sort, gather into the other buffer.
-void enqueue_bin(mdpd_handle* h, bool gather_a)
+// Bin: (first half-kick and drift,) count, scan, scatter, rank inside each
+// cell by id, gather into the other buffer.
+void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
 {
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
-    // count[] is zero here: cleared at creation and by every cell sort
+    // count[] is zero here: cleared at creation and by every scan
     if (h->nrep)
-        launch_bin_count_batch(st, h->cap, h->x[h->cur], h->batch(), h->cellof, h->slot, h->count,
-                               h->status);
+        launch_bin_count_batch(st, h->cap, h->batch(), master(h, h->cur), kick, h->cellof,
+                               h->slot, h->count, h->status);
     else
-        launch_bin_count(st, n, h->cap, h->x[h->cur], h->geo, h->cellof, h->slot, h->count,
-                         h->status);
-    launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp);
+        launch_bin_count(st, n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur), kick, h->cellof,
+                         h->slot, h->count, h->status);
+    launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp, true);
     launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src);
-    launch_cell_sort(st, h->geo.ncell, h->start, h->key, h->src, h->count);
     if (h->nrep)
-        launch_gather_batch(st, h->precision, h->cap, h->src, h->cellof, master(h, h->cur),
-                            master(h, 1 - h->cur), gather_a, h->batch(), h->pos4, h->vel4,
-                            h->cell_s);
+        launch_rank_gather_batch(st, h->precision, h->cap, h->cellof, h->start, h->key, h->src,
+                                 master(h, h->cur), master(h, 1 - h->cur), gather_a, h->batch(),
+                                 h->pos4, h->vel4, h->cell_s);
     else
-        launch_gather(st, h->precision, n, h->cap, h->src, h->cellof, master(h, h->cur),
-                      master(h, 1 - h->cur), gather_a, h->geo, h->pos4, h->vel4, h->cell_s);
+        launch_rank_gather(st, h->precision, n, h->cap, h->cellof, h->start, h->key, h->src,
+                           master(h, h->cur), master(h, 1 - h->cur), gather_a, h->geo, h->pos4,
+                           h->vel4, h->cell_s);
     h->cur = 1 - h->cur;
+}
+
+// Kernel launches of one time step (enqueue_step): count, scan, scatter,
+// rank + gather, density, force, reduction.
+int step_launches(const mdpd_handle* h)
+{
+    return 6 + scan_num_launches(h->geo.ncell);
 }
 
 void enqueue_density(mdpd_handle* h)
@@ -433,14 +445,15 @@ void enqueue_density(mdpd_handle* h)
                        h->start, h->rho);
 }
 
-void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
+void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out, int advance = 0)
 {
     if (h->nrep)
         launch_force_nl_batch(h->stream, h->precision, mode, h->cap, h->batch(), h->pos4, h->vel4,
                               h->rho, h->cell_s, h->start, h->nl, h->nl_count, h->step,
                               step_offset, master(h, h->cur), out, h->partials, h->status);
     else if (h->kernels != MDPD_KERNELS_SCAN)
-        launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
+        launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph,
+                        h->force_lpp, h->mk,
                         h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->nl, h->nl_count,
                         h->step, step_offset, master(h, h->cur), out, h->partials, h->status);
     else
@@ -452,21 +465,24 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out)
 void enqueue_reduce(mdpd_handle* h, int advance)
 {
     if (h->nrep) {
-        launch_reduce_obs_batch(h->stream, h->partials, h->nchunk * PAIR_BLOCK_WARPS, h->d_wr,
-                                h->nrep, h->red_ticket, h->obs_b, h->step, advance);
+        launch_reduce_obs_batch(h->stream, h->precision, h->partials, h->nchunk * PAIR_BLOCK_WARPS,
+                                h->d_wr, h->nrep, h->red_ticket, h->obs_b, h->step, advance);
         return;
     }
-    launch_reduce_obs(h->stream, h->partials, obs_num_partials((int)h->n), h->red_l1,
+    const int lpp = h->kernels == MDPD_KERNELS_SCAN ? 1 : h->force_lpp;
+    launch_reduce_obs(h->stream, h->precision, h->partials, obs_num_partials((int)h->n, lpp),
+                      h->red_l1,
                       h->red_ticket, h->obs, h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS,
                       h->step, advance);
 }
 
-// One velocity-Verlet step after the first half-kick and drift:
-// bin, density, force (+ half-kick [+ next half-kick, drift]), reduction.
-void enqueue_step(mdpd_handle* h, ForceMode mode, cudaEvent_t* evs)
+// One velocity-Verlet step: bin (after the first half-kick and drift when
+// `kick`; otherwise the previous step's force pass did them), density, force
+// (+ half-kick [+ next half-kick, drift]), reduction.
+void enqueue_step(mdpd_handle* h, ForceMode mode, bool kick, cudaEvent_t* evs)
 {
     record(h, evs, 0);
-    enqueue_bin(h, false);
+    enqueue_bin(h, false, kick);
     record(h, evs, 1);
     enqueue_density(h);
     record(h, evs, 2);
@@ -475,8 +491,6 @@ void enqueue_step(mdpd_handle* h, ForceMode mode, cudaEvent_t* evs)
     enqueue_reduce(h, 1);
     record(h, evs, 4);
 }
-
-constexpr int LAUNCHES_PER_STEP = 10;
 
 // Density and forces at the current state (no integration); the result goes
 // to `out` (3 * cap doubles, cell order) or, if out is NULL, to the
@@ -491,13 +505,13 @@ int evaluate(mdpd_handle* h, double* out, bool keep_a)
     return MDPD_OK;
 }
 
-int capture_step(mdpd_handle* h, int prof, int mode, int cur)
+int capture_step(mdpd_handle* h, int prof, int mode, int cur, int kick)
 {
-    Graphs& gg = h->g[prof][mode][cur];
+    Graphs& gg = h->g[prof][mode][cur][kick];
     const int saved = h->cur;
     h->cur = cur;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(h, mode == 0 ? FM_FUSED : FM_LAST, prof ? h->tev : nullptr);
+    enqueue_step(h, mode == 0 ? FM_FUSED : FM_LAST, kick != 0, prof ? h->tev : nullptr);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     h->cur = saved;
@@ -537,20 +551,20 @@ cudaEvent_t* next_prof_events(mdpd_handle* h)
     return evs;
 }
 
-int run_step(mdpd_handle* h, ForceMode mode)
+int run_step(mdpd_handle* h, ForceMode mode, bool kick)
 {
     cudaEvent_t* evs = next_prof_events(h);
-    h->prof_launches += LAUNCHES_PER_STEP;
+    h->prof_launches += step_launches(h);
     if (!h->use_graph) {
-        enqueue_step(h, mode, evs);
+        enqueue_step(h, mode, kick, evs);
         CK(cudaGetLastError());
         return MDPD_OK;
     }
     const int prof = evs ? 1 : 0;
     const int mi = mode == FM_FUSED ? 0 : 1;
-    Graphs& gg = h->g[prof][mi][h->cur];
+    Graphs& gg = h->g[prof][mi][h->cur][kick ? 1 : 0];
     if (!gg.exec) {
-        int rc = capture_step(h, prof, mi, h->cur);
+        int rc = capture_step(h, prof, mi, h->cur, kick ? 1 : 0);
         if (rc) return rc;
     }
     if (prof)
@@ -1024,15 +1038,10 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return MDPD_OK;
-    if (h->nrep)
-        launch_kick_drift_batch(h->stream, h->cap, h->batch(), master(h, h->cur), h->status);
-    else
-        launch_kick_drift(h->stream, (int)h->n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur),
-                          h->status);
-    h->prof_launches += 1;
-    CK(cudaGetLastError());
+    // the first step's binning applies the first half-kick and drift; later
+    // steps get them from the previous force pass (FM_FUSED)
     for (int64_t k = 0; k < nsteps; ++k) {
-        int rc = run_step(h, k + 1 < nsteps ? FM_FUSED : FM_LAST);
+        int rc = run_step(h, k + 1 < nsteps ? FM_FUSED : FM_LAST, k == 0);
         if (rc) return rc;
     }
     h->steps_host += nsteps;
@@ -1247,6 +1256,15 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         h->prof_tick = 0;
         return MDPD_OK;
     }
+    case MDPD_OPT_FORCE_LANES:
+        if (value != 1 && value != 2 && value != 4)
+            return h->fail(MDPD_ERR_INVALID_ARG, "lanes per particle must be 1, 2 or 4");
+        if (h->nrep && value != 1)
+            return h->fail(MDPD_ERR_INVALID_ARG, "a batch runs one lane per particle");
+        CK(cudaStreamSynchronize(h->stream));
+        h->force_lpp = (int)value;
+        destroy_graphs(h);
+        return MDPD_OK;
     case MDPD_OPT_WALL_DENSITY:
         if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "a batch has no walls");
         CK(cudaStreamSynchronize(h->stream));
@@ -1387,39 +1405,68 @@ int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
     if (reps < 1) reps = 5;
     int rc = sync_check(h);
     if (rc) return rc;
-    const int variants[2] = { MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD };
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // mean time of reps launches of `run` after one warm-up, or < 0 on error
+    auto time_it = [&](auto&& run) -> double {
+        run();
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < reps; ++r) run();
+        cudaEventRecord(e1, h->stream);
+        float t = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+            return -1.0;
+        return (double)t / reps;
+    };
+    auto done = [&](int code, const char* what) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return code ? h->fail(code, std::string("autotune: ") + what) : MDPD_OK;
+    };
+    // 1) density variant
+    const int variants[2] = { MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD };
     int best = h->kernels;
     double best_ms = 1e300;
+    enqueue_bin(h, true);                     // same positions: same order, state kept
     for (int v = 0; v < 2; ++v) {
         h->kernels = variants[v];
-        enqueue_bin(h, true);                 // same positions: same order, state kept
-        enqueue_density(h);                   // warm-up
-        cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < reps; ++r) enqueue_density(h);
-        cudaEventRecord(e1, h->stream);
-        cudaError_t e = cudaEventSynchronize(e1);
-        float t = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
-        if (e != cudaSuccess) {
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return h->fail(MDPD_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(e));
-        }
-        if (ms) ms[v] = t / reps;
+        const double t = time_it([&] { enqueue_density(h); });
+        if (t < 0) return done(MDPD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+        if (ms) ms[v] = t;
         if (t < best_ms) {
             best_ms = t;
             best = variants[v];
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     h->kernels = best;
-    destroy_graphs(h);
     enqueue_density(h);                       // rho and lists from the chosen variant
-    if (chosen) *chosen = best;
+    // 2) lanes per particle of the force pass (evaluation only: the state is kept)
+    const int lanes[3] = { 1, 2, 4 };
+    int best_l = h->force_lpp;
+    best_ms = 1e300;
+    for (int v = 0; v < 3; ++v) {
+        if (h->nrep && lanes[v] != 1) {
+            if (ms) ms[2 + v] = -1.0;
+            continue;
+        }
+        h->force_lpp = lanes[v];
+        const double t = time_it([&] { enqueue_force(h, FM_EVAL, 0, h->fout); });
+        if (t < 0) return done(MDPD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+        if (ms) ms[2 + v] = t;
+        if (t < best_ms) {
+            best_ms = t;
+            best_l = lanes[v];
+        }
+    }
+    h->force_lpp = best_l;
+    destroy_graphs(h);
+    if (chosen) {
+        chosen[0] = best;
+        chosen[1] = best_l;
+    }
+    rc = done(MDPD_OK, "");
+    if (rc) return rc;
     return sync_check(h);
 }
 
@@ -1428,7 +1475,7 @@ int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (ncell)
         for (int k = 0; k < 3; ++k) ncell[k] = h->geo.nc[k];
-    if (launches_per_step) *launches_per_step = LAUNCHES_PER_STEP;
+    if (launches_per_step) *launches_per_step = step_launches(h);
     return MDPD_OK;
 }
 

@@ -38,17 +38,18 @@ k_force_vjp(int n, int64_t cap, Geo geo, Phys ph, const typename Vec4<T>::type* 
     for (int k = threadIdx.x; k < 3 * 64; k += blockDim.x) tsh[k] = 0.0;
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
-        shift[c][0] = (T)(c % 3 - 1) * (T)geo.h[0];
-        shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
-        shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
+        shift[c][0] = (T)(c % 3 - 1) * derived<T>(ph).h[0];
+        shift[c][1] = (T)((c / 3) % 3 - 1) * derived<T>(ph).h[1];
+        shift[c][2] = (T)(c / 9 - 1) * derived<T>(ph).h[2];
     }
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s < n) {
         const uint64_t step = *step_ptr;
-        const T rc = (T)ph.rc, rd = (T)ph.rd;
-        const T inv_rc = T(1) / rc, inv_rd = T(1) / rd;
-        const T inv_sqrt_dt = (T)(1.0 / sqrt(ph.dt));
+        const Derived<T>& dc = derived<T>(ph);
+        const T inv_rc = dc.inv_rc, inv_rd = dc.inv_rd;
+        const T rd = (T)ph.rd;
+        const T inv_sqrt_dt = dc.inv_sqrt_dt;
         const V pi = pos4[s];
         const V vi = vel4[s];
         const T rho_i = rho[s];
@@ -134,15 +135,16 @@ k_density_vjp(int n, int64_t cap, Geo geo, Phys ph, const typename Vec4<T>::type
     __shared__ T shift[27][3];
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
-        shift[c][0] = (T)(c % 3 - 1) * (T)geo.h[0];
-        shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
-        shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
+        shift[c][0] = (T)(c % 3 - 1) * derived<T>(ph).h[0];
+        shift[c][1] = (T)((c / 3) % 3 - 1) * derived<T>(ph).h[1];
+        shift[c][2] = (T)(c / 9 - 1) * derived<T>(ph).h[2];
     }
     __syncthreads();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const T rd = (T)ph.rd, inv_rd = T(1) / rd;
-    const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
+    const Derived<T>& dc = derived<T>(ph);
+    const T rd = (T)ph.rd, inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
     const V pi = pos4[s];
     const T rb_i = (T)rbar[s];
     T g[3] = { T(0), T(0), T(0) };

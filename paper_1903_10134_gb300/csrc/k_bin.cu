@@ -1,10 +1,10 @@
-// Cell binning by a stable counting sort (per step): cell id of every
-// particle, per-cell counts, exclusive scan, scatter, a per-cell sort of the
-// slots by particle id (so the order inside a cell does not depend on the
-// order of the atomics), and a gather of the state into cell order with
+// Cell binning by a counting sort (per step): cell id of every particle (with
+// the step's first half-kick and drift when asked), per-cell counts, an
+// exclusive scan, a scatter in atomic order, and one kernel that ranks each
+// particle inside its cell by id (so the order inside a cell does not depend
+// on the order of the atomics) and gathers the state into that order with
 // positions re-expressed as offsets from the cell centre.
-#include "mdpd_internal.cuh"
-#include "vec.cuh"
+#include "pair.cuh"
 
 namespace mdpd {
 
@@ -16,9 +16,11 @@ inline unsigned nblocks(int64_t n, int b = BLOCK) { return (unsigned)((n + b - 1
 
 // Batched kernels (BATCH = true) take their replica from the chunk of the
 // block (see Batch); single-system kernels index by the global thread id.
-template <bool BATCH>
-__global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Geo geo_p, Batch bt,
-                            uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
+// KICK: first apply the step's first half-kick, drift and reflection to the
+// particle (the work of a separate kick launch at the start of mdpd_step).
+template <bool BATCH, bool KICK>
+__global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
+                            Master m, uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
                             uint32_t* __restrict__ count, uint32_t* __restrict__ status)
 {
     pdl_enter();
@@ -28,7 +30,7 @@ __global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Ge
     const Rep* rp = nullptr;
     if constexpr (BATCH) {
         const int4 ch = bt.chunks[blockIdx.x];
-        rp = &block_rep<REP_GEO>(bt.reps, ch.x);
+        rp = &block_rep<KICK ? REP_SCALARS : REP_GEO>(bt.reps, ch.x);
         i = ch.y + (int)threadIdx.x;
         valid = (int)threadIdx.x < ch.z;
         cell0 = rp->cell0;
@@ -38,11 +40,12 @@ __global__ void k_bin_count(int n, int64_t cap, const double* __restrict__ x, Ge
     }
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
+    if constexpr (KICK) kick_drift_one(i, cap, geo, BATCH ? rp->ph : ph_p, mk, m, status);
     int q[3];
     uint32_t st = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        const double xk = x[k * cap + i];
+        const double xk = m.x[k * cap + i];
         if (!isfinite(xk)) {
             st |= ST_NONFINITE;
             q[k] = 0;
@@ -108,34 +111,32 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_blocks(const uint32_t* __
     if (threadIdx.x == 0) sums[blockIdx.x] = total;
 }
 
-// One block: exclusive scan of the nb block sums in place; sums[nb] = total.
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(uint32_t* __restrict__ sums, int nb)
-{
-    pdl_enter();
-    const int base = threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS], s = 0;
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        v[k] = base + k < nb ? sums[base + k] : 0u;
-        s += v[k];
-    }
-    uint32_t total;
-    uint32_t run = block_exclusive(s, &total);
-#pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < nb) sums[base + k] = run;
-        run += v[k];
-    }
-    if (threadIdx.x == 0) sums[nb] = total;
-}
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __restrict__ in,
+// Second pass: block b first adds the sums of the blocks before it (each
+// block does this itself, so no third launch scans the block sums), then
+// writes its tile's exclusive prefix.  Block 0 writes out[n], the total.
+// zero_in: clear in[] after reading it.
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(uint32_t* __restrict__ in,
                                                              int64_t n,
                                                              const uint32_t* __restrict__ sums,
-                                                             int nb, uint32_t* __restrict__ out)
+                                                             int nb, uint32_t* __restrict__ out,
+                                                             int zero_in)
 {
     pdl_enter();
-    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    __shared__ uint32_t before_sh;
+    const int b = (int)blockIdx.x;
+    uint32_t mine = 0, all = 0;
+    for (int q = threadIdx.x; q < nb; q += SCAN_THREADS) {
+        const uint32_t t = sums[q];
+        mine += q < b ? t : 0u;
+        all += t;
+    }
+    uint32_t tot;
+    block_exclusive(mine, &tot);
+    if (threadIdx.x == 0) before_sh = tot;
+    uint32_t grand;
+    block_exclusive(all, &grand);
+    const uint32_t before = before_sh;
+    const int64_t base = (int64_t)b * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS], s = 0;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
@@ -143,13 +144,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const uint32_t* __r
         s += v[k];
     }
     uint32_t total;
-    uint32_t run = block_exclusive(s, &total) + sums[blockIdx.x];
+    uint32_t run = block_exclusive(s, &total) + before;
 #pragma unroll
     for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < n) out[base + k] = run;
+        if (base + k < n) {
+            out[base + k] = run;
+            if (zero_in) in[base + k] = 0u;
+        }
         run += v[k];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = sums[nb];
+    if (b == 0 && threadIdx.x == 0) out[n] = grand;
 }
 
 __global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
@@ -189,14 +193,24 @@ __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
     }
 }
 
+// Order inside each cell by particle id, fused with the gather into cell
+// order.  The scatter filled slot a (in atomic order) with key[a] = id and
+// src[a] = the particle's master index i; the particle's place in its cell c
+// is s = start[c] + (number of keys of the cell below key[a]), and the thread
+// copies particle i's master state to slot s of the other buffer and writes
+// the compute arrays of slot s: position as FP32/FP64 offset from the cell
+// centre with the type bits, velocity with the id (within the replica).
 template <typename T, bool BATCH>
-__global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
-                         const uint32_t* __restrict__ cellof, Master in, Master out,
-                         int gather_a, Geo geo_p, Batch bt, typename Vec4<T>::type* __restrict__ pos4,
-                         typename Vec4<T>::type* __restrict__ vel4, uint32_t* __restrict__ cell_s)
+__global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ cellof,
+                              const uint32_t* __restrict__ start, const uint32_t* __restrict__ key,
+                              const uint32_t* __restrict__ src, Master in, Master out,
+                              int gather_a, Geo geo_p, Batch bt,
+                              typename Vec4<T>::type* __restrict__ pos4,
+                              typename Vec4<T>::type* __restrict__ vel4,
+                              uint32_t* __restrict__ cell_s)
 {
     pdl_enter();
-    int s;
+    int a;
     bool valid;
     int64_t cell0 = 0;
     uint32_t id0 = 0;
@@ -204,18 +218,24 @@ __global__ void k_gather(int n, int64_t cap, const uint32_t* __restrict__ src,
     if constexpr (BATCH) {
         const int4 ch = bt.chunks[blockIdx.x];
         rp = &block_rep<REP_GEO>(bt.reps, ch.x);
-        s = ch.y + (int)threadIdx.x;
+        a = ch.y + (int)threadIdx.x;
         valid = (int)threadIdx.x < ch.z;
         cell0 = rp->cell0;
         id0 = rp->id0;
     } else {
-        s = blockIdx.x * blockDim.x + threadIdx.x;
-        valid = s < n;
+        a = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = a < n;
     }
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
-    const uint32_t i = src[s];
-    const uint32_t c = cellof[i] - (uint32_t)cell0;      // cell within the replica
+    const uint32_t i = src[a];
+    const uint32_t cg = cellof[i];
+    const uint32_t b = start[cg], e = start[cg + 1];
+    const uint32_t kk = key[a];
+    uint32_t r = 0;
+    for (uint32_t q = b; q < e; ++q) r += key[q] < kk ? 1u : 0u;
+    const uint32_t s = b + r;
+    const uint32_t c = cg - (uint32_t)cell0;      // cell within the replica
     const int q[3] = { (int)(c % (uint32_t)geo.nc[0]),
                        (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]),
                        (int)(c / ((uint32_t)geo.nc[0] * (uint32_t)geo.nc[1])) };
@@ -316,32 +336,36 @@ __global__ void k_scatter_type_by_id(int n, const uint32_t* __restrict__ id,
 
 }  // namespace
 
-void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, const Geo& geo,
-                      uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
+void launch_bin_count(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
+                      const MaskDev& mk, const Master& m, bool kick, uint32_t* cellof,
+                      uint32_t* slot, uint32_t* count, uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_bin_count<false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, x, geo, Batch{},
-               cellof, slot, count, status);
+    launch_pdl(kick ? k_bin_count<false, true> : k_bin_count<false, false>, dim3(nblocks(n)),
+               dim3(BLOCK), st, n, cap, geo, ph, Batch{}, mk, m, cellof, slot, count, status);
 }
 
-void launch_bin_count_batch(cudaStream_t st, int64_t cap, const double* x, const Batch& bt,
-                            uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status)
+void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
+                            bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
+                            uint32_t* status)
 {
     if (bt.nchunk <= 0) return;
-    launch_pdl_smem(k_bin_count<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
-                    x, Geo{}, bt, cellof, slot, count, status);
+    launch_pdl_smem(kick ? k_bin_count<true, true> : k_bin_count<true, false>, dim3(bt.nchunk),
+                    dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap, Geo{}, Phys{}, bt, MaskDev{}, m,
+                    cellof, slot, count, status);
 }
 
 int scan_num_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
-void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint32_t* out,
-                           uint32_t* tmp)
+int scan_num_launches(int64_t) { return 2; }
+
+void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
+                           bool zero_in)
 {
     const int nb = scan_num_blocks(n);
     if (nb <= 0) return;
     launch_pdl(k_scan_blocks, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp);
-    launch_pdl(k_scan_top, dim3(1), dim3(SCAN_THREADS), st, tmp, nb);
-    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp, nb, out);
+    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp, nb, out, (int)zero_in);
 }
 
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
@@ -358,31 +382,36 @@ void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uin
     launch_pdl(k_cell_sort, dim3(nblocks(ncell)), dim3(BLOCK), st, ncell, start, key, src, count);
 }
 
-void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
-                   const uint32_t* cellof, const Master& in, const Master& out, bool gather_a,
-                   const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s)
+void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
+                        const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
+                        const uint32_t* src, const Master& in, const Master& out, bool gather_a,
+                        const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s)
 {
     if (n <= 0) return;
     if (precision == 0)
-        launch_pdl(k_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof,
-                   in, out, (int)gather_a, geo, Batch{}, (D4*)pos4, (D4*)vel4, cell_s);
+        launch_pdl(k_rank_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
+                   start, key, src, in, out, (int)gather_a, geo, Batch{}, (D4*)pos4, (D4*)vel4,
+                   cell_s);
     else
-        launch_pdl(k_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, src, cellof,
-                   in, out, (int)gather_a, geo, Batch{}, (float4*)pos4, (float4*)vel4, cell_s);
+        launch_pdl(k_rank_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
+                   start, key, src, in, out, (int)gather_a, geo, Batch{}, (float4*)pos4,
+                   (float4*)vel4, cell_s);
 }
 
-void launch_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* src,
-                         const uint32_t* cellof, const Master& in, const Master& out,
-                         bool gather_a, const Batch& bt, void* pos4, void* vel4, uint32_t* cell_s)
+void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
+                              const uint32_t* start, const uint32_t* key, const uint32_t* src,
+                              const Master& in, const Master& out, bool gather_a, const Batch& bt,
+                              void* pos4, void* vel4, uint32_t* cell_s)
 {
     if (bt.nchunk <= 0) return;
     const dim3 g(bt.nchunk), b(BATCH_CHUNK);
     if (precision == 0)
-        launch_pdl_smem(k_gather<double, true>, g, b, REP_SMEM, st, 0, cap, src, cellof, in, out,
-                        (int)gather_a, Geo{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
+        launch_pdl_smem(k_rank_gather<double, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
+                        src, in, out, (int)gather_a, Geo{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
     else
-        launch_pdl_smem(k_gather<float, true>, g, b, REP_SMEM, st, 0, cap, src, cellof, in, out,
-                        (int)gather_a, Geo{}, bt, (float4*)pos4, (float4*)vel4, cell_s);
+        launch_pdl_smem(k_rank_gather<float, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
+                        src, in, out, (int)gather_a, Geo{}, bt, (float4*)pos4, (float4*)vel4,
+                        cell_s);
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,

@@ -55,17 +55,18 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
     const Phys& ph = BATCH ? rp->ph : ph_p;
-    const T rd2 = (T)(ph.rd * ph.rd), rc2 = (T)(ph.rc * ph.rc);
-    const T inv_rd = (T)(1.0 / ph.rd);
-    const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
+    const Derived<T>& dc = derived<T>(ph);
+    const T rd2 = dc.rd2, rc2 = dc.rc2;
+    const T inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
     const auto pi = pos4[s];
     const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     const bool mobile = ph.list_all || mob_true;
     // wall density of a mobile particle (WANT_PHI): sum over frozen partners
     // within r_c of 15/(2 pi r_c^3) (1 - r/r_c)^2
     const bool want_phi = WANT_PHI && mob_true;
-    const T inv_rc = (T)(1.0 / ph.rc);
-    const T cphi = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rc * ph.rc * ph.rc));
+    const T inv_rc = dc.inv_rc;
+    const T cphi = dc.cw_phi;
     T phi = T(0);
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
@@ -74,15 +75,15 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
         if (z < 0) continue;
-        const T sz = pi.z - (T)oz * (T)geo.h[2];
+        const T sz = pi.z - (T)oz * dc.h[2];
         for (int oy = -1; oy <= 1; ++oy) {
             const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
             if (y < 0) continue;
-            const T sy = pi.y - (T)oy * (T)geo.h[1];
+            const T sy = pi.y - (T)oy * dc.h[1];
             for (int ox = -1; ox <= 1; ++ox) {
                 const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
                 if (x < 0) continue;
-                const T sx = pi.x - (T)ox * (T)geo.h[0];
+                const T sx = pi.x - (T)ox * dc.h[0];
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
                 const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
                 const uint32_t b = start[nc], e = start[nc + 1];
@@ -184,10 +185,11 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     if (lane == 27) pre[w][27] = C;
     __syncwarp();
 
-    const T rc2 = (T)(ph.rc * ph.rc);
-    const T inv_rd = (T)(1.0 / ph.rd);
-    const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
-    const T hx = (T)geo.h[0], hy = (T)geo.h[1], hz = (T)geo.h[2];
+    const Derived<T>& dc = derived<T>(ph);
+    const T rc2 = dc.rc2;
+    const T inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
+    const T hx = dc.h[0], hy = dc.h[1], hz = dc.h[2];
     const unsigned lt = (1u << lane) - 1u;
 
     for (uint32_t g0 = hb; g0 < he; g0 += DC_GROUP) {
@@ -281,14 +283,21 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
 #ifndef MDPD_FORCE_MIN_BLOCKS
 #define MDPD_FORCE_MIN_BLOCKS 8
 #endif
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, int LPP>
 constexpr int force_min_blocks()
 {
-    return sizeof(T) != 4 ? 0 : (BATCH ? MDPD_FORCE_BATCH_MIN_BLOCKS : MDPD_FORCE_MIN_BLOCKS);
+    // several lanes per particle hold the group reduction's values too: 4 blocks
+    return sizeof(T) != 4 ? 0
+                          : (BATCH ? MDPD_FORCE_BATCH_MIN_BLOCKS
+                                   : (LPP > 1 ? 4 : MDPD_FORCE_MIN_BLOCKS));
 }
 
-template <typename T, int MODE, bool BATCH>
-__global__ void __launch_bounds__(PAIR_BLOCK, (force_min_blocks<T, BATCH>()))
+// LPP lanes share one particle: lane `sub` of the group takes the list
+// entries sub, sub + LPP, ...; the group's sums are combined with a fixed
+// butterfly.  LPP > 1 multiplies the warps of a small system (a 48k-particle
+// slab fills only 2.5 blocks per SM at one lane per particle).
+template <typename T, int MODE, bool BATCH, int LPP>
+__global__ void __launch_bounds__(PAIR_BLOCK, (force_min_blocks<T, BATCH, LPP>()))
 k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
            const typename Vec4<T>::type* __restrict__ pos4,
            const typename Vec4<T>::type* __restrict__ vel4, const T* __restrict__ rho,
@@ -299,6 +308,9 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
 {
     pdl_enter();
     using V = typename Vec4<T>::type;
+    static_assert(LPP == 1 || LPP == 2 || LPP == 4, "lanes per particle");
+    static_assert(!BATCH || LPP == 1, "a batch chunk is one particle per lane");
+    constexpr int PPB = PAIR_BLOCK / LPP;        // particles per block
     __shared__ PairTables<T> tab;
     __shared__ T shift[27][3];
     __shared__ int act[PAIR_BLOCK];
@@ -316,17 +328,18 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
         in_range = (int)threadIdx.x < ch.z;
         cell0 = rp->cell0;
     } else {
-        s0 = blockIdx.x * PAIR_BLOCK + threadIdx.x;
-        in_range = s0 < n;
+        s0 = blockIdx.x * PPB + threadIdx.x;
+        in_range = (int)threadIdx.x < PPB && s0 < n;
     }
     const Geo& geo = BATCH ? rp->geo : geo_p;
     const Phys& ph = BATCH ? rp->ph : ph_p;      // in a batch: scalars only (see block_rep)
     load_tables(tab, BATCH ? bt.reps[rep_r].ph : ph_p);
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
-        shift[c][0] = (T)(c % 3 - 1) * (T)geo.h[0];
-        shift[c][1] = (T)((c / 3) % 3 - 1) * (T)geo.h[1];
-        shift[c][2] = (T)(c / 9 - 1) * (T)geo.h[2];
+        const Derived<T>& dc = derived<T>(ph);
+        shift[c][0] = (T)(c % 3 - 1) * dc.h[0];
+        shift[c][1] = (T)((c / 3) % 3 - 1) * dc.h[1];
+        shift[c][2] = (T)(c / 9 - 1) * dc.h[2];
     }
     // compact the block's mobile particles onto the first lanes, in cell order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -348,11 +361,16 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
     __syncthreads();
 
     const uint64_t step = *step_ptr + (uint64_t)step_offset;
-    double obs[NOBS];
+    T obs[NOBS];
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) obs[k] = 0.0;
-    if ((int)threadIdx.x < nact) {
-        const int s = act[threadIdx.x];
+    for (int k = 0; k < NOBS; ++k) obs[k] = T(0);
+    const int slot = (int)threadIdx.x / LPP, sub = (int)threadIdx.x % LPP;
+    const bool active = slot < nact;
+    const int s = active ? act[slot] : 0;
+    T f[3] = { T(0), T(0), T(0) };
+    T W[6] = { T(0), T(0), T(0), T(0), T(0), T(0) };
+    int npair = 0;
+    if (active) {
         const PairConst<T> c(ph);
         const V pi = pos4[s];
         const V vi = vel4[s];
@@ -363,18 +381,16 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
         const T* tB = tab.B + ti * 8;
         const T* tG = tab.G + ti * 8;
         const T* tS = tab.S + ti * 8;
-        T f[3] = { T(0), T(0), T(0) };
-        T W[6] = { T(0), T(0), T(0), T(0), T(0), T(0) };
-        int npair = 0;
         const uint32_t cnt = nl_count[s];
         if (cnt <= (uint32_t)NL_MAX) {
-            uint32_t e0 = cnt > 0 ? nl[s] : 0u;
-            uint32_t e1 = cnt > 1 ? nl[cap + s] : 0u;
+            const uint32_t k0 = (uint32_t)sub;
+            uint32_t e0 = k0 < cnt ? nl[(int64_t)k0 * cap + s] : 0u;
+            uint32_t e1 = k0 + LPP < cnt ? nl[(int64_t)(k0 + LPP) * cap + s] : 0u;
             V pj = pos4[e0 >> 5];
             V vj = vel4[e0 >> 5];
             T rj = rho[e0 >> 5];
-            for (uint32_t k = 0; k < cnt; ++k) {
-                const uint32_t e2 = k + 2 < cnt ? nl[(int64_t)(k + 2) * cap + s] : 0u;
+            for (uint32_t k = k0; k < cnt; k += LPP) {
+                const uint32_t e2 = k + 2 * LPP < cnt ? nl[(int64_t)(k + 2 * LPP) * cap + s] : 0u;
                 const V pn = pos4[e1 >> 5];
                 const V vn = vel4[e1 >> 5];
                 const T rn = rho[e1 >> 5];
@@ -391,8 +407,9 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                 vj = vn;
                 rj = rn;
             }
-            npair = (int)cnt;
-        } else {
+            npair = sub == 0 ? (int)cnt : 0;
+        } else if (sub == 0) {
+            // more partners than list slots: scan the 27 neighbour cells
             int q0, q1, q2;
             cell_coords(cell_s[s], geo, q0, q1, q2);
             for (int oz = -1; oz <= 1; ++oz) {
@@ -425,12 +442,24 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                 }
             }
         }
-        force_finish<T, MODE>(s, true, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     }
+    if constexpr (LPP > 1) {
+        // every lane of the warp takes part (inactive groups add zeros)
+#pragma unroll
+        for (int o = 1; o < LPP; o <<= 1) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) f[k] += __shfl_xor_sync(0xffffffffu, f[k], o);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) W[k] += __shfl_xor_sync(0xffffffffu, W[k], o);
+            npair += __shfl_xor_sync(0xffffffffu, npair, o);
+        }
+    }
+    if (active && sub == 0)
+        force_finish<T, MODE>(s, true, f, W, npair, cap, geo, ph, mk, m, out, obs, status);
     warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
-template <typename T, bool BATCH>
+template <typename T, bool BATCH, int LPP>
 void launch_force_nl_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const Batch& bt, const MaskDev& mk, const void* pos4,
                        const void* vel4, const void* rho, const uint32_t* cell_s,
@@ -439,19 +468,41 @@ void launch_force_nl_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, cons
                        double* partials, uint32_t* status)
 {
     using V = typename Vec4<T>::type;
-    const int nb = BATCH ? bt.nchunk : force_num_blocks(n);
+    const int nb = BATCH ? bt.nchunk : force_num_blocks(n, LPP);
     const size_t smem = BATCH ? REP_SMEM : 0;
     const V* p = (const V*)pos4;
     const V* v = (const V*)vel4;
     const T* r = (const T*)rho;
 #define MDPD_FNL(MODE_)                                                                    \
-    launch_pdl_smem(k_force_nl<T, MODE_, BATCH>, dim3(nb), dim3(PAIR_BLOCK), smem, st, n, cap, \
-                    geo, ph, bt, mk, p, v, r, cell_s, start, nl, nl_count, step_ptr,       \
+    launch_pdl_smem(k_force_nl<T, MODE_, BATCH, LPP>, dim3(nb), dim3(PAIR_BLOCK), smem, st, n, \
+                    cap, geo, ph, bt, mk, p, v, r, cell_s, start, nl, nl_count, step_ptr,    \
                     step_offset, m, out, partials, status)
     if (mode == FM_EVAL) MDPD_FNL(FM_EVAL);
     else if (mode == FM_LAST) MDPD_FNL(FM_LAST);
     else MDPD_FNL(FM_FUSED);
 #undef MDPD_FNL
+}
+
+template <typename T>
+void launch_force_nl_lpp(cudaStream_t st, ForceMode mode, int n, int64_t cap, const Geo& geo,
+                         const Phys& ph, int lpp, const MaskDev& mk, const void* pos4,
+                         const void* vel4, const void* rho, const uint32_t* cell_s,
+                         const uint32_t* start, const uint32_t* nl, const uint32_t* nl_count,
+                         const uint64_t* step_ptr, int step_offset, const Master& m, double* out,
+                         double* partials, uint32_t* status)
+{
+    if (lpp == 4)
+        launch_force_nl_t<T, false, 4>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
+                                       cell_s, start, nl, nl_count, step_ptr, step_offset, m, out,
+                                       partials, status);
+    else if (lpp == 2)
+        launch_force_nl_t<T, false, 2>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
+                                       cell_s, start, nl, nl_count, step_ptr, step_offset, m, out,
+                                       partials, status);
+    else
+        launch_force_nl_t<T, false, 1>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
+                                       cell_s, start, nl, nl_count, step_ptr, step_offset, m, out,
+                                       partials, status);
 }
 
 }  // namespace
@@ -516,20 +567,20 @@ void launch_density_cell_batch(cudaStream_t st, int precision, int64_t cap, cons
 }
 
 void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
-                     const Geo& geo, const Phys& ph, const MaskDev& mk, const void* pos4,
+                     const Geo& geo, const Phys& ph, int lpp, const MaskDev& mk, const void* pos4,
                      const void* vel4, const void* rho, const uint32_t* cell_s,
                      const uint32_t* start, const uint32_t* nl, const uint32_t* nl_count,
                      const uint64_t* step_ptr, int step_offset, const Master& m, double* out,
                      double* partials, uint32_t* status)
 {
     if (precision == 0)
-        launch_force_nl_t<double, false>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
-                                         cell_s, start, nl, nl_count, step_ptr, step_offset, m,
-                                         out, partials, status);
+        launch_force_nl_lpp<double>(st, mode, n, cap, geo, ph, lpp, mk, pos4, vel4, rho, cell_s,
+                                    start, nl, nl_count, step_ptr, step_offset, m, out, partials,
+                                    status);
     else
-        launch_force_nl_t<float, false>(st, mode, n, cap, geo, ph, Batch{}, mk, pos4, vel4, rho,
-                                        cell_s, start, nl, nl_count, step_ptr, step_offset, m,
-                                        out, partials, status);
+        launch_force_nl_lpp<float>(st, mode, n, cap, geo, ph, lpp, mk, pos4, vel4, rho, cell_s,
+                                   start, nl, nl_count, step_ptr, step_offset, m, out, partials,
+                                   status);
 }
 
 void launch_force_nl_batch(cudaStream_t st, int precision, ForceMode mode, int64_t cap,
@@ -541,11 +592,11 @@ void launch_force_nl_batch(cudaStream_t st, int precision, ForceMode mode, int64
     const MaskDev none{};
     if (bt.nchunk <= 0) return;
     if (precision == 0)
-        launch_force_nl_t<double, true>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
+        launch_force_nl_t<double, true, 1>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
                                         cell_s, start, nl, nl_count, step_ptr, step_offset, m,
                                         out, partials, status);
     else
-        launch_force_nl_t<float, true>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
+        launch_force_nl_t<float, true, 1>(st, mode, 0, cap, Geo{}, Phys{}, bt, none, pos4, vel4, rho,
                                        cell_s, start, nl, nl_count, step_ptr, step_offset, m,
                                        out, partials, status);
 }

@@ -21,9 +21,10 @@ k_density(int n, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ po
     pdl_enter();
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    const T rd2 = (T)(ph.rd * ph.rd);
-    const T inv_rd = (T)(1.0 / ph.rd);
-    const T cw = (T)(15.0 / (2.0 * 3.14159265358979323846 * ph.rd * ph.rd * ph.rd));
+    const Derived<T>& dc = derived<T>(ph);
+    const T rd2 = dc.rd2;
+    const T inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
     const auto pi = pos4[s];
     const uint32_t c = cell_s[s];
     const int q0 = (int)(c % (uint32_t)geo.nc[0]);
@@ -36,21 +37,21 @@ k_density(int n, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ po
             if (!geo.periodic[2]) continue;
             z = z < 0 ? z + geo.nc[2] : z - geo.nc[2];
         }
-        const T sz = pi.z - (T)oz * (T)geo.h[2];
+        const T sz = pi.z - (T)oz * derived<T>(ph).h[2];
         for (int oy = -1; oy <= 1; ++oy) {
             int y = q1 + oy;
             if (y < 0 || y >= geo.nc[1]) {
                 if (!geo.periodic[1]) continue;
                 y = y < 0 ? y + geo.nc[1] : y - geo.nc[1];
             }
-            const T sy = pi.y - (T)oy * (T)geo.h[1];
+            const T sy = pi.y - (T)oy * derived<T>(ph).h[1];
             for (int ox = -1; ox <= 1; ++ox) {
                 int x = q0 + ox;
                 if (x < 0 || x >= geo.nc[0]) {
                     if (!geo.periodic[0]) continue;
                     x = x < 0 ? x + geo.nc[0] : x - geo.nc[0];
                 }
-                const T sx = pi.x - (T)ox * (T)geo.h[0];
+                const T sx = pi.x - (T)ox * derived<T>(ph).h[0];
                 const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
                 const uint32_t b = start[nc], e = start[nc + 1];
                 for (uint32_t j = b; j < e; ++j) {
@@ -88,9 +89,9 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     __syncthreads();
     const uint64_t step = *step_ptr + (uint64_t)step_offset;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    double obs[NOBS];
+    T obs[NOBS];
 #pragma unroll
-    for (int k = 0; k < NOBS; ++k) obs[k] = 0.0;
+    for (int k = 0; k < NOBS; ++k) obs[k] = T(0);
     if (s < n) {
         const PairConst<T> c(ph);
         const auto pi = pos4[s];
@@ -112,15 +113,15 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
             for (int oz = -1; oz <= 1; ++oz) {
                 const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
                 if (z < 0) continue;
-                const T sz = pi.z - (T)oz * (T)geo.h[2];
+                const T sz = pi.z - (T)oz * derived<T>(ph).h[2];
                 for (int oy = -1; oy <= 1; ++oy) {
                     const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
                     if (y < 0) continue;
-                    const T sy = pi.y - (T)oy * (T)geo.h[1];
+                    const T sy = pi.y - (T)oy * derived<T>(ph).h[1];
                     for (int ox = -1; ox <= 1; ++ox) {
                         const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
                         if (x < 0) continue;
-                        const T sx = pi.x - (T)ox * (T)geo.h[0];
+                        const T sx = pi.x - (T)ox * derived<T>(ph).h[0];
                         const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
                         const uint32_t b = start[nc], e = start[nc + 1];
                         for (uint32_t j = b; j < e; ++j) {
@@ -143,107 +144,120 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
     warp_obs_store(obs, partials, (int64_t)gridDim.x * (PAIR_BLOCK / 32));
 }
 
-template <bool BATCH>
-__global__ void k_kick_drift(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
-                             Master m, uint32_t* __restrict__ status)
+// Reduction of the per-warp observable partials (type P: the pair
+// arithmetic's precision).  FP64 additions, and conversions from FP64, cost
+// 64 FP32 operations on this part, so the partials are added in P with the
+// block's threads in parallel and only the 16 column sums per observable are
+// widened to FP64.  Every addition happens in a fixed order, so the result is
+// reproducible.
+constexpr int RED_THREADS = 256;
+constexpr int RED_CHUNK = RED_THREADS * 16;   // partials per level-one block
+
+// res[k] = sum over q in [q0, q1) of data[k * stride + q], for the NOBS
+// observables: thread t adds q = q0 + t, q0 + t + RED_THREADS, ...; then 16
+// threads per observable add 16 columns each; then one thread per observable
+// adds the 16 results in FP64.  The two counts (mobile particles, pairs) are
+// added as 64-bit integers, so they stay exact at any size.  res is valid
+// for every thread on return.
+template <typename P>
+__device__ void block_sum_obs(const P* __restrict__ data, int64_t stride, int64_t q0, int64_t q1,
+                              double* res)
+{
+    constexpr int NV = NOBS - 2;
+    __shared__ P sh[NV][RED_THREADS + 1];
+    __shared__ unsigned long long shc[2][RED_THREADS + 1];
+    __shared__ P s16[NV][16];
+    __shared__ unsigned long long s16c[2][16];
+    P v[NV];
+    unsigned long long c[2] = { 0ull, 0ull };
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = P(0);
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += RED_THREADS) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] += __ldcg(&data[(int64_t)k * stride + q]);
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+            c[k] += bits_count<P>(__ldcg(&data[(int64_t)(NV + k) * stride + q]));
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = v[k];
+    shc[0][threadIdx.x] = c[0];
+    shc[1][threadIdx.x] = c[1];
+    __syncthreads();
+    if (threadIdx.x < NOBS * 16) {
+        const int k = threadIdx.x >> 4, part = threadIdx.x & 15;
+        if (k < NV) {
+            P a = P(0);
+#pragma unroll
+            for (int l = 0; l < RED_THREADS / 16; ++l) a += sh[k][part * (RED_THREADS / 16) + l];
+            s16[k][part] = a;
+        } else {
+            unsigned long long a = 0ull;
+#pragma unroll
+            for (int l = 0; l < RED_THREADS / 16; ++l) a += shc[k - NV][part * (RED_THREADS / 16) + l];
+            s16c[k - NV][part] = a;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < NOBS) {
+        const int k = threadIdx.x;
+        if (k < NV) {
+            double a = 0.0;
+#pragma unroll
+            for (int l = 0; l < 16; ++l) a += (double)s16[k][l];
+            res[k] = a;
+        } else {
+            unsigned long long a = 0ull;
+#pragma unroll
+            for (int l = 0; l < 16; ++l) a += s16c[k - NV][l];
+            res[k] = (double)a;
+        }
+    }
+    __syncthreads();
+}
+
+// One block over all nparts partials.
+template <typename P>
+__global__ void __launch_bounds__(RED_THREADS)
+k_reduce_obs_small(const P* __restrict__ partials, int nparts, double* __restrict__ obs,
+                   double* __restrict__ obs_sum, double* __restrict__ obs_count,
+                   uint64_t* __restrict__ step_ptr, int advance)
 {
     pdl_enter();
-    int s;
-    bool valid;
-    const Rep* rp = nullptr;
-    if constexpr (BATCH) {
-        const int4 ch = bt.chunks[blockIdx.x];
-        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
-        s = ch.y + (int)threadIdx.x;
-        valid = (int)threadIdx.x < ch.z;
-    } else {
-        s = blockIdx.x * blockDim.x + threadIdx.x;
-        valid = s < n;
-    }
-    if (!valid) return;
-    const Geo& geo = BATCH ? rp->geo : geo_p;
-    const Phys& ph = BATCH ? rp->ph : ph_p;
-    if ((ph.frozen >> m.type[s]) & 1u) return;
-    double x[3], v[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        x[k] = m.x[k * cap + s];
-        v[k] = __dadd_rn(m.v[k * cap + s], __dmul_rn(ph.hdt, m.a[k * cap + s]));
-    }
-    drift_reflect(x, v, geo, mk, ph.dt);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        m.x[k * cap + s] = x[k];
-        m.v[k * cap + s] = v[k];
-    }
-    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) atomicOr(status, ST_NONFINITE);
-}
-
-// Final reduction of the observables, one launch in two levels.  FP64 adds
-// run at a small fraction of the FP32 rate on this part, so the sums are laid
-// out to do few of them: block b takes the per-warp partials
-// [b * RED_CHUNK, (b + 1) * RED_CHUNK), one per thread, transposes them
-// through shared memory, and 16 threads per observable add 16 values each
-// before one thread adds those 16 results; the block writes its level-one
-// partial and takes a ticket.  The block holding the last ticket adds the
-// level-one partials in block order, derives the observables, accumulates the
-// running sums, advances the step counter when asked and resets the ticket.
-// Every addition happens in a fixed order, so the result is reproducible.
-constexpr int RED_CHUNK = 256;
-constexpr int RED_THREADS = RED_CHUNK;
-
-// Observables from the summed partials t (momentum 3, sum v^2 3, virial 6,
-// mobile count, pairs): o = momentum, kinetic energy, kT, virial, sum v^2,
-// mobile count, step; obs[2 * MDPD_NUM_OBS + 1] = the directed pair count.
-__device__ void finish_obs(const double (&t)[NOBS], uint64_t step, double* __restrict__ obs,
-                           double* __restrict__ obs_sum, double* __restrict__ obs_count,
-                           int advance)
-{
-    double o[MDPD_NUM_OBS];
-    for (int k = 0; k < 3; ++k) o[k] = t[k];
-    o[3] = 0.5 * (t[3] + t[4] + t[5]);
-    const double nm = t[12];
-    o[4] = nm > 1.0 ? 2.0 * o[3] / (3.0 * (nm - 1.0)) : 0.0;
-    for (int k = 0; k < 6; ++k) o[5 + k] = t[6 + k];
-    for (int k = 0; k < 3; ++k) o[11 + k] = t[3 + k];
-    o[14] = nm;
-    o[15] = (double)step;
-    for (int k = 0; k < MDPD_NUM_OBS; ++k) obs[k] = o[k];
-    obs[2 * MDPD_NUM_OBS + 1] = t[13];     // directed pairs with r < r_c
-    if (advance) {
-        for (int k = 0; k < MDPD_NUM_OBS; ++k) obs_sum[k] += o[k];
-        *obs_count += 1.0;
+    __shared__ double res[NOBS];
+    block_sum_obs<P>(partials, nparts, 0, nparts, res);
+    if (threadIdx.x == 0) {
+        double t[NOBS];
+        for (int k = 0; k < NOBS; ++k) t[k] = res[k];
+        const uint64_t step = *step_ptr + (advance ? 1u : 0u);
+        finish_obs(t, step, obs, obs_sum, obs_count, advance);
+        if (advance) *step_ptr = step;
     }
 }
 
+// Two levels in one launch: block b reduces the partials
+// [b * RED_CHUNK, (b + 1) * RED_CHUNK) to a level-one partial l1[k * nb + b]
+// and takes a ticket; the block with the last ticket reduces the level-one
+// partials, derives the observables, accumulates the running sums, advances
+// the step counter when asked and resets the ticket.
+template <typename P>
 __global__ void __launch_bounds__(RED_THREADS)
-k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict__ l1,
+k_reduce_obs(const P* __restrict__ partials, int nparts, P* __restrict__ l1,
              unsigned* __restrict__ ticket, double* __restrict__ obs,
              double* __restrict__ obs_sum, double* __restrict__ obs_count,
              uint64_t* __restrict__ step_ptr, int advance)
 {
     pdl_enter();
-    __shared__ double sh[NOBS][RED_CHUNK + 1];
-    __shared__ double s16[NOBS][17];
+    __shared__ double res[NOBS];
     __shared__ bool last;
-    const int b = blockIdx.x * RED_CHUNK + threadIdx.x;
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k)
-        sh[k][threadIdx.x] = b < nparts ? partials[(int64_t)k * nparts + b] : 0.0;
-    __syncthreads();
-    if (threadIdx.x < NOBS * 16) {
-        const int k = threadIdx.x >> 4, part = threadIdx.x & 15;
-        double v = 0.0;
-#pragma unroll
-        for (int l = 0; l < RED_CHUNK / 16; ++l) v += sh[k][part * (RED_CHUNK / 16) + l];
-        s16[k][part] = v;
-    }
-    __syncthreads();
+    const int64_t q0 = (int64_t)blockIdx.x * RED_CHUNK;
+    const int64_t q1 = q0 + RED_CHUNK < nparts ? q0 + RED_CHUNK : nparts;
+    block_sum_obs<P>(partials, nparts, q0, q1, res);
     if (threadIdx.x < NOBS) {
-        double v = 0.0;
-#pragma unroll
-        for (int l = 0; l < 16; ++l) v += s16[threadIdx.x][l];
-        l1[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
+        // counts keep the integer bit pattern (at most RED_CHUNK * 2048 < 2^32)
+        const int k = threadIdx.x;
+        l1[(int64_t)k * gridDim.x + blockIdx.x] =
+            k < NOBS - 2 ? (P)res[k] : count_bits<P>((unsigned)res[k]);
     }
     __threadfence();
     __syncthreads();
@@ -251,15 +265,10 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (threadIdx.x < NOBS) {
-        double v = 0.0;
-        for (unsigned q = 0; q < gridDim.x; ++q) v += __ldcg(&l1[(int64_t)threadIdx.x * gridDim.x + q]);
-        s16[threadIdx.x][16] = v;
-    }
-    __syncthreads();
+    block_sum_obs<P>(l1, gridDim.x, 0, gridDim.x, res);
     if (threadIdx.x == 0) {
         double t[NOBS];
-        for (int k = 0; k < NOBS; ++k) t[k] = s16[k][16];
+        for (int k = 0; k < NOBS; ++k) t[k] = res[k];
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
         finish_obs(t, step, obs, obs_sum, obs_count, advance);
         if (advance) *step_ptr = step;
@@ -267,44 +276,24 @@ k_reduce_obs(const double* __restrict__ partials, int nparts, double* __restrict
     }
 }
 
-// Per-replica reduction of a batch: block r adds the per-warp partials of
-// replica r's chunks, [wr[r].x, wr[r].y), in a fixed order (a strided sum per
-// thread, then 16 partial sums per observable, then one), and writes the
-// replica's observables to obs[r * OBS_STRIDE ...] (current values, running
-// sums, count, pairs: the layout of a single system).  The block holding the
-// last ticket advances the shared step counter.
+// Per-replica reduction of a batch: block r reduces the partials of replica
+// r's chunks, [wr[r].x, wr[r].y), and writes the replica's observables to
+// obs[r * OBS_STRIDE ...] (current values, running sums, count, pairs: the
+// layout of a single system).  The block holding the last ticket advances the
+// shared step counter.
+template <typename P>
 __global__ void __launch_bounds__(RED_THREADS)
-k_reduce_obs_batch(const double* __restrict__ partials, int nparts, const int2* __restrict__ wr,
+k_reduce_obs_batch(const P* __restrict__ partials, int nparts, const int2* __restrict__ wr,
                    unsigned* __restrict__ ticket, double* __restrict__ obs,
                    uint64_t* __restrict__ step_ptr, int advance)
 {
     pdl_enter();
-    __shared__ double sh[NOBS][RED_THREADS + 1];
-    __shared__ double s16[NOBS][17];
+    __shared__ double res[NOBS];
     const int2 w = wr[blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < NOBS; ++k) {
-        double v = 0.0;
-        for (int q = w.x + (int)threadIdx.x; q < w.y; q += RED_THREADS)
-            v += partials[(int64_t)k * nparts + q];
-        sh[k][threadIdx.x] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < NOBS * 16) {
-        const int k = threadIdx.x >> 4, part = threadIdx.x & 15;
-        double v = 0.0;
-#pragma unroll
-        for (int l = 0; l < RED_THREADS / 16; ++l) v += sh[k][part * (RED_THREADS / 16) + l];
-        s16[k][part] = v;
-    }
-    __syncthreads();
+    block_sum_obs<P>(partials, nparts, w.x, w.y, res);
     if (threadIdx.x == 0) {
         double t[NOBS];
-        for (int k = 0; k < NOBS; ++k) {
-            double v = 0.0;
-            for (int l = 0; l < 16; ++l) v += s16[k][l];
-            t[k] = v;
-        }
+        for (int k = 0; k < NOBS; ++k) t[k] = res[k];
         const uint64_t step = *step_ptr + (advance ? 1u : 0u);
         double* o = obs + (int64_t)blockIdx.x * OBS_STRIDE;
         finish_obs(t, step, o, o + MDPD_NUM_OBS, o + 2 * MDPD_NUM_OBS, advance);
@@ -350,9 +339,13 @@ void launch_force_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const G
 
 }  // namespace
 
-int force_num_blocks(int n) { return n > 0 ? (n + PAIR_BLOCK - 1) / PAIR_BLOCK : 1; }
+int force_num_blocks(int n, int lpp)
+{
+    const int per = PAIR_BLOCK / lpp;
+    return n > 0 ? (n + per - 1) / per : 1;
+}
 
-int obs_num_partials(int n) { return force_num_blocks(n) * (PAIR_BLOCK / 32); }
+int obs_num_partials(int n, int lpp) { return force_num_blocks(n, lpp) * (PAIR_BLOCK / 32); }
 
 void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const Phys& ph,
                     const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho)
@@ -381,40 +374,43 @@ void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t
                               step_ptr, step_offset, m, out, partials, status);
 }
 
-void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
-                       const MaskDev& mk, const Master& m, uint32_t* status)
-{
-    if (n <= 0) return;
-    launch_pdl(k_kick_drift<false>, dim3((n + 255) / 256), dim3(256), st, n, cap, geo, ph, Batch{},
-               mk, m, status);
-}
-
-void launch_kick_drift_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
-                             uint32_t* status)
-{
-    if (bt.nchunk <= 0) return;
-    launch_pdl_smem(k_kick_drift<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
-                    Geo{}, Phys{}, bt, MaskDev{}, m, status);
-}
-
-void launch_reduce_obs_batch(cudaStream_t st, const double* partials, int nparts, const int2* wr,
-                             int nrep, unsigned* ticket, double* obs, uint64_t* step_ptr,
-                             int advance)
-{
-    if (nrep <= 0) return;
-    launch_pdl(k_reduce_obs_batch, dim3(nrep), dim3(RED_THREADS), st, partials, nparts, wr, ticket,
-               obs, step_ptr, advance);
-}
-
 int reduce_l1_blocks(int nparts) { return (nparts + RED_CHUNK - 1) / RED_CHUNK; }
 
-void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
-                       unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
-                       uint64_t* step_ptr, int advance)
+void launch_reduce_obs(cudaStream_t st, int precision, const double* partials, int nparts,
+                       double* l1, unsigned* ticket, double* obs, double* obs_sum,
+                       double* obs_count, uint64_t* step_ptr, int advance)
 {
-    const int nb = reduce_l1_blocks(nparts) > 0 ? reduce_l1_blocks(nparts) : 1;
-    launch_pdl(k_reduce_obs, dim3(nb), dim3(RED_THREADS), st, partials, nparts, l1, ticket, obs, obs_sum,
-                                             obs_count, step_ptr, advance);
+    // one block when its threads add at most 32 (FP32) or 4 (FP64) partials each
+    const int small_max = precision == 1 ? RED_THREADS * 32 : RED_THREADS * 4;
+    if (nparts <= small_max) {
+        if (precision == 1)
+            launch_pdl(k_reduce_obs_small<float>, dim3(1), dim3(RED_THREADS), st,
+                       (const float*)partials, nparts, obs, obs_sum, obs_count, step_ptr, advance);
+        else
+            launch_pdl(k_reduce_obs_small<double>, dim3(1), dim3(RED_THREADS), st, partials, nparts,
+                       obs, obs_sum, obs_count, step_ptr, advance);
+        return;
+    }
+    const int nb = reduce_l1_blocks(nparts);
+    if (precision == 1)
+        launch_pdl(k_reduce_obs<float>, dim3(nb), dim3(RED_THREADS), st, (const float*)partials,
+                   nparts, (float*)l1, ticket, obs, obs_sum, obs_count, step_ptr, advance);
+    else
+        launch_pdl(k_reduce_obs<double>, dim3(nb), dim3(RED_THREADS), st, partials, nparts, l1,
+                   ticket, obs, obs_sum, obs_count, step_ptr, advance);
+}
+
+void launch_reduce_obs_batch(cudaStream_t st, int precision, const double* partials, int nparts,
+                             const int2* wr, int nrep, unsigned* ticket, double* obs,
+                             uint64_t* step_ptr, int advance)
+{
+    if (nrep <= 0) return;
+    if (precision == 1)
+        launch_pdl(k_reduce_obs_batch<float>, dim3(nrep), dim3(RED_THREADS), st,
+                   (const float*)partials, nparts, wr, ticket, obs, step_ptr, advance);
+    else
+        launch_pdl(k_reduce_obs_batch<double>, dim3(nrep), dim3(RED_THREADS), st, partials, nparts,
+                   wr, ticket, obs, step_ptr, advance);
 }
 
 }  // namespace mdpd

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <cstddef>
 #include <utility>
 
@@ -27,6 +28,21 @@ struct Geo {
     int64_t ncell;
 };
 
+// Constants derived from Phys and Geo in the precision of the pair
+// arithmetic, computed once on the host (FP64 arithmetic runs at a small
+// fraction of the FP32 rate on this part, so kernels must not rederive them
+// per thread).
+template <typename T>
+struct Derived {
+    T rc2, rd2, inv_rc, inv_rd;
+    T cw_rho;        // 15 / (2 pi r_d^3): density weight normalisation (Sec. 2.1)
+    T cw_phi;        // 15 / (2 pi r_c^3): wall-density weight normalisation
+    T inv_sqrt_dt;   // random force scale 1 / sqrt(dt)
+    T h[3];          // cell edges
+    T hdt;           // dt / 2
+    T g[3];          // body force
+};
+
 // Physical constants of Sec. 2.1 / Eq. 1, tables flattened [ti * 8 + tj].
 struct Phys {
     double rc, rd, dt, hdt, kT;
@@ -36,10 +52,48 @@ struct Phys {
     int xi_dist;
     int rho_self;
     int list_all;                 // 1: the density pass lists partners of frozen particles too
+    int prec32;                   // 1: FP32 pair arithmetic (kick increments formed in FP32)
     void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
-    double A[64], B[64], gamma[64], sigma[64];
+    Derived<float> df;
+    Derived<double> dd;
+    double A[64], B[64], gamma[64], sigma[64];   // keep last: a batch copies what precedes A
 };
+
+template <typename T>
+__host__ __device__ __forceinline__ const Derived<T>& derived(const Phys& ph);
+template <>
+__host__ __device__ __forceinline__ const Derived<float>& derived<float>(const Phys& ph) { return ph.df; }
+template <>
+__host__ __device__ __forceinline__ const Derived<double>& derived<double>(const Phys& ph) { return ph.dd; }
+
+// Fill ph.df and ph.dd from ph (rc, rd, dt) and the cell edges.
+inline void fill_derived(Phys& ph, const Geo& geo)
+{
+    const double pi = 3.14159265358979323846;
+    Derived<double>& d = ph.dd;
+    d.rc2 = ph.rc * ph.rc;
+    d.rd2 = ph.rd * ph.rd;
+    d.inv_rc = 1.0 / ph.rc;
+    d.inv_rd = 1.0 / ph.rd;
+    d.cw_rho = 15.0 / (2.0 * pi * ph.rd * ph.rd * ph.rd);
+    d.cw_phi = 15.0 / (2.0 * pi * ph.rc * ph.rc * ph.rc);
+    d.inv_sqrt_dt = ph.dt > 0.0 ? 1.0 / std::sqrt(ph.dt) : 0.0;
+    for (int k = 0; k < 3; ++k) d.h[k] = geo.h[k];
+    d.hdt = 0.5 * ph.dt;
+    for (int k = 0; k < 3; ++k) d.g[k] = ph.g[k];
+    Derived<float>& f = ph.df;
+    f.rc2 = (float)d.rc2;
+    f.rd2 = (float)d.rd2;
+    f.inv_rc = (float)d.inv_rc;
+    f.inv_rd = (float)d.inv_rd;
+    f.cw_rho = (float)d.cw_rho;
+    f.cw_phi = (float)d.cw_phi;
+    f.inv_sqrt_dt = (float)d.inv_sqrt_dt;
+    for (int k = 0; k < 3; ++k) f.h[k] = (float)d.h[k];
+    f.hdt = (float)d.hdt;
+    for (int k = 0; k < 3; ++k) f.g[k] = (float)d.g[k];
+}
 
 // One member of a batch of independent systems: its box and cell lattice,
 // the global index of its first cell and of its first particle, and its
@@ -157,20 +211,34 @@ __device__ __forceinline__ const Rep& block_rep(const Rep* __restrict__ reps, in
 constexpr int OBS_PARTIALS = 16;   // observable slots per partial (14 used)
 
 // ---- launchers (binning / scan) -------------------------------------------
-void launch_bin_count(cudaStream_t st, int n, int64_t cap, const double* x, const Geo& geo,
-                      uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status);
+// Cell of every particle from the master positions m.x, and its arrival rank
+// in the cell (atomic order); kick: first the step's first half-kick, drift
+// and reflection.
+void launch_bin_count(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
+                      const MaskDev& mk, const Master& m, bool kick, uint32_t* cellof,
+                      uint32_t* slot, uint32_t* count, uint32_t* status);
 int scan_num_blocks(int64_t n);
-// Exclusive scan of in[0..n) into out[0..n]; tmp holds scan_num_blocks(n) + 1 words.
-void launch_exclusive_scan(cudaStream_t st, const uint32_t* in, int64_t n, uint32_t* out,
-                           uint32_t* tmp);
+int scan_num_launches(int64_t n);
+// Exclusive scan of in[0..n) into out[0..n]; tmp holds scan_num_blocks(n) + 1
+// words; zero_in clears in[] after it is read.
+void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
+                           bool zero_in = false);
+// For every scattered slot a: the particle's place s in its cell (rank of
+// key[a] = id among the cell's keys), and the gather of master state in[src[a]]
+// to out[s] with the cell-ordered compute arrays (pos4, vel4, cell_s).
+void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
+                        const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
+                        const uint32_t* src, const Master& in, const Master& out, bool gather_a,
+                        const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s);
+void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
+                              const uint32_t* start, const uint32_t* key, const uint32_t* src,
+                              const Master& in, const Master& out, bool gather_a, const Batch& bt,
+                              void* pos4, void* vel4, uint32_t* cell_s);
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
                         const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src);
 // Sorts each cell's slots by key and clears count[] for the next binning.
 void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
                       uint32_t* src, uint32_t* count);
-void launch_gather(cudaStream_t st, int precision, int n, int64_t cap, const uint32_t* src,
-                   const uint32_t* cellof, const Master& in, const Master& out, bool gather_a,
-                   const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s);
 
 // ---- launchers (pair passes) -----------------------------------------------
 void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const Phys& ph,
@@ -180,9 +248,10 @@ void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t
                   const void* vel4, const void* rho, const uint32_t* cell_s,
                   const uint32_t* start, const uint64_t* step_ptr, int step_offset,
                   const Master& m, double* out, double* partials, uint32_t* status);
-int force_num_blocks(int n);
+// Blocks of a force launch over n particles at lpp lanes per particle.
+int force_num_blocks(int n, int lpp = 1);
 // Number of per-warp observable partials the force pass writes for n particles.
-int obs_num_partials(int n);
+int obs_num_partials(int n, int lpp = 1);
 // Density pass that also writes the force partners of mobile particles
 // (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
@@ -192,33 +261,31 @@ void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
                          const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,
                          void* rho, uint32_t* nl, uint32_t* nl_count);
+// lpp: lanes per particle (1, 2 or 4).
 void launch_force_nl(cudaStream_t st, int precision, ForceMode mode, int n, int64_t cap,
-                     const Geo& geo, const Phys& ph, const MaskDev& mk, const void* pos4,
+                     const Geo& geo, const Phys& ph, int lpp, const MaskDev& mk, const void* pos4,
                      const void* vel4, const void* rho, const uint32_t* cell_s,
                      const uint32_t* start, const uint32_t* nl, const uint32_t* nl_count,
                      const uint64_t* step_ptr, int step_offset, const Master& m, double* out,
                      double* partials, uint32_t* status);
 constexpr int NL_SLOTS = 64;      // must equal NL_MAX of the kernels
-void launch_kick_drift(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
-                       const MaskDev& mk, const Master& m, uint32_t* status);
 // Level-one blocks of the observable reduction for nparts partials.
 int reduce_l1_blocks(int nparts);
-// Two-level reduction of the per-warp partials (l1: NOBS * reduce_l1_blocks
-// doubles; ticket: one zero-initialised counter, left at zero).
-void launch_reduce_obs(cudaStream_t st, const double* partials, int nparts, double* l1,
-                       unsigned* ticket, double* obs, double* obs_sum, double* obs_count,
-                       uint64_t* step_ptr, int advance);
+// Reduction of the per-warp partials (stored as FP32 when precision = 1, FP64
+// otherwise; l1: NOBS * reduce_l1_blocks values of that type; ticket: one
+// zero-initialised counter, left at zero).
+void launch_reduce_obs(cudaStream_t st, int precision, const double* partials, int nparts,
+                       double* l1, unsigned* ticket, double* obs, double* obs_sum,
+                       double* obs_count, uint64_t* step_ptr, int advance);
 
 // ---- launchers (batch of replicas; see Batch) ------------------------------
 constexpr int OBS_STRIDE = 2 * MDPD_NUM_OBS + 2;   // per-replica observable record
 void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, const double* vel3,
                              const Batch& bt, const Master& m, const uint8_t* type_by_id,
                              uint32_t* status);
-void launch_bin_count_batch(cudaStream_t st, int64_t cap, const double* x, const Batch& bt,
-                            uint32_t* cellof, uint32_t* slot, uint32_t* count, uint32_t* status);
-void launch_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* src,
-                         const uint32_t* cellof, const Master& in, const Master& out,
-                         bool gather_a, const Batch& bt, void* pos4, void* vel4, uint32_t* cell_s);
+void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
+                            bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
+                            uint32_t* status);
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
                              const void* pos4, const uint32_t* cell_s, const uint32_t* start,
                              void* rho, uint32_t* nl, uint32_t* nl_count);
@@ -231,12 +298,10 @@ void launch_force_nl_batch(cudaStream_t st, int precision, ForceMode mode, int64
                            const uint32_t* cell_s, const uint32_t* start, const uint32_t* nl,
                            const uint32_t* nl_count, const uint64_t* step_ptr, int step_offset,
                            const Master& m, double* out, double* partials, uint32_t* status);
-void launch_kick_drift_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
-                             uint32_t* status);
 // wr[r] = the range of partials of replica r; obs holds nrep * OBS_STRIDE doubles.
-void launch_reduce_obs_batch(cudaStream_t st, const double* partials, int nparts, const int2* wr,
-                             int nrep, unsigned* ticket, double* obs, uint64_t* step_ptr,
-                             int advance);
+void launch_reduce_obs_batch(cudaStream_t st, int precision, const double* partials, int nparts,
+                             const int2* wr, int nrep, unsigned* ticket, double* obs,
+                             uint64_t* step_ptr, int advance);
 
 // ---- launchers (adjoint) ---------------------------------------------------
 // VJP of one force evaluation at the current cell-ordered state (lists built

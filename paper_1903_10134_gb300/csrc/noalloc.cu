@@ -194,6 +194,7 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
     ph.rc = p->rc;
     ph.rd = p->rd;
     ph.rho_self = p->rho_self ? 1 : 0;
+    fill_derived(ph, geo);
     void* base = nullptr;
     int rc = scratch_address(&base, why);
     if (rc) return bad(rc, why);

@@ -53,8 +53,8 @@ template <typename T>
 struct PairConst {
     T rc2, rd2, inv_rc, inv_rd, inv_sqrt_dt;
     __device__ explicit PairConst(const Phys& ph)
-        : rc2((T)(ph.rc * ph.rc)), rd2((T)(ph.rd * ph.rd)), inv_rc((T)(1.0 / ph.rc)),
-          inv_rd((T)(1.0 / ph.rd)), inv_sqrt_dt((T)(1.0 / sqrt(ph.dt)))
+        : rc2(derived<T>(ph).rc2), rd2(derived<T>(ph).rd2), inv_rc(derived<T>(ph).inv_rc),
+          inv_rd(derived<T>(ph).inv_rd), inv_sqrt_dt(derived<T>(ph).inv_sqrt_dt)
     {
     }
 };
@@ -137,81 +137,183 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
     }
 }
 
+// First half-kick, drift and reflection of the particle in master slot s
+// (Algorithm 1: v += dt/2 a, x += dt v); frozen particles stay.
+// With FP32 pair arithmetic the stored acceleration is an FP32 value and the
+// increment is formed in FP32 as in force_finish.
+__device__ __forceinline__ void kick_drift_one(int s, int64_t cap, const Geo& geo, const Phys& ph,
+                                               const MaskDev& mk, const Master& m,
+                                               uint32_t* status)
+{
+    if ((ph.frozen >> m.type[s]) & 1u) return;
+    double x[3], v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        x[k] = m.x[k * cap + s];
+        const double a = m.a[k * cap + s];
+        const double d = ph.prec32 ? (double)(ph.df.hdt * (float)a) : __dmul_rn(ph.hdt, a);
+        v[k] = __dadd_rn(m.v[k * cap + s], d);
+    }
+    drift_reflect(x, v, geo, mk, ph.dt);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        m.x[k * cap + s] = x[k];
+        m.v[k * cap + s] = v[k];
+    }
+    if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) atomicOr(status, ST_NONFINITE);
+}
+
 // Everything after the pair sum of mobile-or-frozen particle s: acceleration,
-// the half-kick(s), drift and reflection by MODE, and the observables.
+// the half-kick(s), drift and reflection by MODE, and the observables (in T).
+//
+// FP64 pair arithmetic (T = double) takes every step in FP64 with separately
+// rounded products and sums.  With FP32 pair arithmetic the forces carry FP32
+// rounding anyway, so the kick increment dv = (dt/2) a is formed in FP32 and
+// applied to the FP64 master velocity with one conversion and one add per
+// component; FP64 instructions run at 1/64 of the FP32 rate on this part,
+// and this keeps the epilogue close to the drift's cost.
 template <typename T, int MODE>
 __device__ __forceinline__ void force_finish(int s, bool mobile, const T (&f)[3],
                                              const T (&W)[6], int npair, int64_t cap,
                                              const Geo& geo, const Phys& ph, const MaskDev& mk,
                                              const Master& m, double* __restrict__ out,
-                                             double (&obs)[NOBS], uint32_t* status)
+                                             T (&obs)[NOBS], uint32_t* status)
 {
-    double a[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) a[k] = mobile ? (double)f[k] + ph.g[k] : 0.0;
     uint32_t st = 0;
-    if (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[2])) st |= ST_NONFINITE;
-    double v[3];
+    if constexpr (sizeof(T) == 8) {
+        double a[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
-    if (MODE == FM_EVAL) {
+        for (int k = 0; k < 3; ++k) a[k] = mobile ? (double)f[k] + ph.g[k] : 0.0;
+        if (!isfinite(a[0]) || !isfinite(a[1]) || !isfinite(a[2])) st |= ST_NONFINITE;
+        double v[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) out[k * cap + s] = a[k];
-    } else if (mobile) {
+        for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
+        if (MODE == FM_EVAL) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
+            for (int k = 0; k < 3; ++k) out[k * cap + s] = a[k];
+        } else if (mobile) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
+        }
+        if (mobile) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                obs[k] = v[k];
+                obs[3 + k] = v[k] * v[k];
+            }
+        }
+        if (MODE == FM_LAST && mobile) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                m.v[k * cap + s] = v[k];
+                m.a[k * cap + s] = a[k];
+            }
+        }
+        if (MODE == FM_FUSED && mobile) {
+            double x[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                x[k] = m.x[k * cap + s];
+                v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
+            }
+            drift_reflect(x, v, geo, mk, ph.dt);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                m.x[k * cap + s] = x[k];
+                m.v[k * cap + s] = v[k];
+            }
+        }
+        if (MODE != FM_EVAL && (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])))
+            st |= ST_NONFINITE;
+    } else {
+        const Derived<float>& dc = ph.df;
+        float af[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) af[k] = mobile ? f[k] + dc.g[k] : 0.f;
+        if (!isfinite(af[0]) || !isfinite(af[1]) || !isfinite(af[2])) st |= ST_NONFINITE;
+        double v[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
+        if (MODE == FM_EVAL) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) out[k * cap + s] = (double)af[k];
+        }
+        if (mobile) {
+            float dv[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dv[k] = MODE == FM_EVAL ? 0.f : dc.hdt * af[k];
+                const float v1 = (float)v[k] + dv[k];          // v(t + dt)
+                obs[k] = v1;
+                obs[3 + k] = v1 * v1;
+            }
+            if (MODE == FM_LAST) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    m.v[k * cap + s] = __dadd_rn(v[k], (double)dv[k]);
+                    m.a[k * cap + s] = (double)af[k];
+                }
+            }
+            if (MODE == FM_FUSED) {
+                // the same two adds as FM_LAST followed by the next step's
+                // first kick (kick_drift_one), so split and fused steps agree
+                double x[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    x[k] = m.x[k * cap + s];
+                    const double d = (double)dv[k];
+                    v[k] = __dadd_rn(__dadd_rn(v[k], d), d);
+                }
+                drift_reflect(x, v, geo, mk, ph.dt);
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    m.x[k * cap + s] = x[k];
+                    m.v[k * cap + s] = v[k];
+                }
+            }
+        }
     }
     if (mobile) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            obs[k] = v[k];
-            obs[3 + k] = v[k] * v[k];
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) obs[6 + k] = (double)W[k];
-        obs[12] = 1.0;
-        obs[13] = (double)npair;
+        for (int k = 0; k < 6; ++k) obs[6 + k] = W[k];
+        obs[12] = T(1);
+        obs[13] = (T)npair;
     }
-    if (MODE == FM_LAST && mobile) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            m.v[k * cap + s] = v[k];
-            m.a[k * cap + s] = a[k];
-        }
-    }
-    if (MODE == FM_FUSED && mobile) {
-        double x[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            x[k] = m.x[k * cap + s];
-            v[k] = __dadd_rn(v[k], __dmul_rn(ph.hdt, a[k]));
-        }
-        drift_reflect(x, v, geo, mk, ph.dt);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            m.x[k * cap + s] = x[k];
-            m.v[k * cap + s] = v[k];
-        }
-    }
-    if (MODE != FM_EVAL && (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])))
-        st |= ST_NONFINITE;
     if (st) atomicOr(status, st);
 }
 
-// Per-warp partial sums of the observables, written to
-// partials[k * nparts + global warp index] with no block-wide barrier, so a
-// warp that finishes early does not hold its block.  FP64 arithmetic is slow
-// on this part, so the FP64 values are transposed through shared memory and
-// summed serially by a few lanes (16 values per lane, then one combining
-// add) instead of a shuffle tree in which every lane adds at every level;
-// the two integer counts use the warp integer reduction.  The order of the
-// additions is fixed, so the result is reproducible.
+// Per-warp partial sums of the observables, written as T to
+// partials[k * nparts + global warp index] with no block-wide barrier,
+// so a warp that finishes early does not hold its block.  The values are
+// transposed through shared memory and summed serially by a few lanes (16
+// values per lane, then one combining add) instead of a shuffle tree in which
+// every lane adds at every level; with FP32 pair arithmetic these 32-term
+// sums and the stored partials are FP32 (FP64 instructions, conversions
+// included, are slow on this part).  The two integer counts use the warp
+// integer reduction and are stored as integer bit patterns.
+// The order of the additions is fixed, so the result is reproducible.
 constexpr int NOBS_F = 12;   // momentum 3, sum v^2 3, virial 6
 
-__device__ __forceinline__ void warp_obs_store(const double (&o)[NOBS], double* __restrict__ partials,
+// The two count partials travel as the bit pattern of an unsigned integer in
+// a T slot (no conversion instructions; read back with bits_count).
+template <typename T>
+__device__ __forceinline__ T count_bits(unsigned c)
+{
+    if constexpr (sizeof(T) == 4) return __uint_as_float(c);
+    else return __longlong_as_double((long long)c);
+}
+template <typename T>
+__device__ __forceinline__ unsigned long long bits_count(T x)
+{
+    if constexpr (sizeof(T) == 4) return (unsigned long long)__float_as_uint(x);
+    else return (unsigned long long)__double_as_longlong(x);
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_obs_store(const T (&o)[NOBS], double* __restrict__ partials,
                                                int64_t nparts)
 {
-    __shared__ double sh[PAIR_BLOCK / 32][NOBS_F][33];
+    __shared__ T sh[PAIR_BLOCK / 32][NOBS_F][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int k = 0; k < NOBS_F; ++k) sh[warp][k][lane] = o[k];
@@ -219,17 +321,42 @@ __device__ __forceinline__ void warp_obs_store(const double (&o)[NOBS], double* 
     const unsigned np = __reduce_add_sync(0xffffffffu, (unsigned)o[13]);
     __syncwarp();
     const int k = lane & 15, half = lane >> 4;
-    double v = 0.0;
+    T v = T(0);
     if (k < NOBS_F) {
 #pragma unroll
         for (int l = 0; l < 16; ++l) v += sh[warp][k][16 * half + l];
     }
     v += __shfl_down_sync(0xffffffffu, v, 16);
     const int64_t gw = (int64_t)blockIdx.x * (PAIR_BLOCK / 32) + warp;
-    if (lane < NOBS_F) partials[(int64_t)lane * nparts + gw] = v;
+    T* p = reinterpret_cast<T*>(partials);
+    if (lane < NOBS_F) p[(int64_t)lane * nparts + gw] = v;
     if (lane == 0) {
-        partials[(int64_t)12 * nparts + gw] = (double)nm;
-        partials[(int64_t)13 * nparts + gw] = (double)np;
+        p[(int64_t)12 * nparts + gw] = count_bits<T>(nm);
+        p[(int64_t)13 * nparts + gw] = count_bits<T>(np);
+    }
+}
+
+// Observables from the summed partials t (momentum 3, sum v^2 3, virial 6,
+// mobile count, pairs): o = momentum, kinetic energy, kT, virial, sum v^2,
+// mobile count, step; obs[2 * MDPD_NUM_OBS + 1] = the directed pair count.
+__device__ __forceinline__ void finish_obs(const double (&t)[NOBS], uint64_t step,
+                                           double* __restrict__ obs, double* __restrict__ obs_sum,
+                                           double* __restrict__ obs_count, int advance)
+{
+    double o[MDPD_NUM_OBS];
+    for (int k = 0; k < 3; ++k) o[k] = t[k];
+    o[3] = 0.5 * (t[3] + t[4] + t[5]);
+    const double nm = t[12];
+    o[4] = nm > 1.0 ? 2.0 * o[3] / (3.0 * (nm - 1.0)) : 0.0;
+    for (int k = 0; k < 6; ++k) o[5 + k] = t[6 + k];
+    for (int k = 0; k < 3; ++k) o[11 + k] = t[3 + k];
+    o[14] = nm;
+    o[15] = (double)step;
+    for (int k = 0; k < MDPD_NUM_OBS; ++k) obs[k] = o[k];
+    obs[2 * MDPD_NUM_OBS + 1] = t[13];     // directed pairs with r < r_c
+    if (advance) {
+        for (int k = 0; k < MDPD_NUM_OBS; ++k) obs_sum[k] += o[k];
+        *obs_count += 1.0;
     }
 }
 

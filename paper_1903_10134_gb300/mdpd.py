@@ -25,6 +25,7 @@ OPT_PROFILE = 2
 OPT_KERNELS = 3
 OPT_PROFILE_EVERY = 4
 OPT_WALL_DENSITY = 5
+OPT_FORCE_LANES = 6
 KERNELS_NLIST = 0
 KERNELS_SCAN = 1
 KERNELS_NLIST_THREAD = 2
@@ -134,7 +135,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_profile.argtypes = [P, P, C.POINTER(i64), C.POINTER(i64)]
     L.mdpd_describe.argtypes = [P, P, C.POINTER(i32)]
     L.mdpd_density_noalloc.argtypes = [P, i64, P, P, P]
-    L.mdpd_autotune.argtypes = [P, i32, C.POINTER(i32), P]
+    L.mdpd_autotune.argtypes = [P, i32, P, P]
     L.mdpd_set_params.argtypes = [P, P]
     L.mdpd_get_wall_density.argtypes = [P, P]
     L.mdpd_set_step.argtypes = [P, i64]
@@ -382,13 +383,25 @@ def mdpd_force_vjp_dev(h, abar_t, xbar_t=None, ubar_t=None, theta_bar_t=None):
                                     _tptr(theta_bar_t)), h)
 
 
-def mdpd_autotune(h, reps: int = 5):
-    """Pick the faster density-pass variant on the current state; returns
-    (chosen variant, [ms of each variant])."""
-    chosen = C.c_int32()
-    ms = np.zeros(2)
-    _check(lib().mdpd_autotune(h, int(reps), C.byref(chosen), _p(ms)), h)
-    return int(chosen.value), ms.tolist()
+class Tuned(tuple):
+    """Result of mdpd_autotune: unpacks as (density variant, [ms per variant]);
+    .lanes is the force pass's lanes per particle, .force_ms its times at 1, 2,
+    4 lanes (-1: not tried)."""
+
+    def __new__(cls, chosen, ms):
+        t = super().__new__(cls, (int(chosen[0]), [float(x) for x in ms[:2]]))
+        t.lanes = int(chosen[1])
+        t.force_ms = [float(x) for x in ms[2:]]
+        return t
+
+
+def mdpd_autotune(h, reps: int = 5) -> Tuned:
+    """Pick the faster density-pass variant, then the fastest lanes per
+    particle of the force pass, on the current state."""
+    chosen = np.zeros(2, np.int32)
+    ms = np.zeros(5)
+    _check(lib().mdpd_autotune(h, int(reps), _p(chosen), _p(ms)), h)
+    return Tuned(chosen, ms)
 
 
 def mdpd_density_noalloc(params, pos_t, rho_t, stream=None):

@@ -65,8 +65,10 @@ def test_batch_members_match_standalone_bitwise(M, precision, kernels):
         assert np.array_equal(x, xs) and np.array_equal(v, vs), r
         assert np.array_equal(rho, rhos), r
         assert np.array_equal(t, w.type)
-        # the observables are reduced in another order: equal to rounding
-        assert np.allclose(obs[r], obs_s, rtol=1e-12, atol=1e-12 * np.abs(obs_s).max()), r
+        # the observables are reduced in another order (a single system with
+        # FP32 pair arithmetic adds its FP32 warp sums in FP32): equal to rounding
+        tol = 1e-12 if precision == 0 else 2e-6
+        assert np.allclose(obs[r], obs_s, rtol=tol, atol=tol * np.abs(obs_s).max()), r
         assert obs[r][15] == K
     b.close()
 
@@ -96,8 +98,10 @@ def test_batch_graph_direct_autotune_and_set_state(M):
     assert np.array_equal(b1.state()[0], b2.state()[0])
     # autotune keeps the state and the trajectory stays that of the chosen variant
     x0, v0, _, _ = b1.state()
-    chosen, ms = b1.autotune(3)
+    res = b1.autotune(3)
+    chosen, ms = res
     assert chosen in (M.KERNELS_NLIST, M.KERNELS_NLIST_THREAD) and len(ms) == 2
+    assert res.lanes == 1 and res.force_ms[1:] == [-1.0, -1.0]
     x1, v1, _, _ = b1.state()
     assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
     # set_state: each replica restarts from the given state (forces re-evaluated
