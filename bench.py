@@ -37,6 +37,9 @@ NUM_SMS = 152
 # Philox-4x32-10 ten rounds of 2 mul-hi + 2 mul-lo + 2 xor = 60, counter 2,
 # xi 4, F^R 3, sum 2, scale 1, accumulate 3.
 OPS_PER_PAIR = 100
+# Hand count for one candidate test of the density pass (Sec. 2.1): separation
+# 3, r^2 3, cutoff compare 1, select 1.
+OPS_PER_CANDIDATE = 8
 
 DESC = {
     "slab": "liquid-vapour slab, periodic 60x20x20, 20x20x20 liquid block at density 6, "
@@ -180,23 +183,69 @@ def _oracle_walls(w) -> dict:
     return {"mask": w.mask, "voxel": w.voxel, "origin": w.origin}
 
 
-def force_traffic(workload: str, precision: str):
-    """DRAM bytes per force-pass launch from the committed ncu summary, or None
-    when there is none for this workload or the kernel sources changed since
-    the counters were taken (the summary records their SHA-1)."""
+def kernel_traffic(workload: str, precision: str) -> dict:
+    """DRAM bytes per launch of each profiled kernel from the committed ncu
+    summary profiles/traffic_<workload>.txt ({} when there is none, the
+    precision is not FP32, or a source file of that kernel changed since the
+    counters were taken: each kernel line carries the SHA-1 of its sources)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", f"force_traffic_{workload}.json")
+    path = os.path.join(ROOT, "profiles", f"traffic_{workload}.txt")
     if precision != "fp32" or not os.path.exists(path):
-        return None
+        return {}
+    out = {}
     try:
-        d = json.load(open(path))
-        h = hashlib.sha1()
-        for src in d["sources"]:
-            with open(os.path.join(ROOT, src), "rb") as f:
-                h.update(f.read())
-        return d["dram_bytes_per_launch"] if h.hexdigest() == d["source_sha1"] else None
-    except (OSError, ValueError, KeyError):
-        return None
+        for line in open(path):
+            # kernel <name> bytes <n> sha1 <hex> sources <a,b,...>
+            f = line.split()
+            if len(f) < 8 or f[0] != "kernel":
+                continue
+            h = hashlib.sha1()
+            for src in f[7].split(","):
+                with open(os.path.join(ROOT, src), "rb") as fh:
+                    h.update(fh.read())
+            if h.hexdigest() == f[5]:
+                out[f[1]] = int(f[3])
+    except (OSError, ValueError):
+        return {}
+    return out
+
+
+def candidate_tests(x, params, ncell) -> int:
+    """Candidate tests of one density pass: every particle is tested against
+    every particle of its 27 neighbour cells (itself included), so the count
+    is sum over cells c of n_c times the particles in c's neighbourhood."""
+    import numpy as np
+    nc = np.array(ncell, dtype=np.int64)
+    lo = np.array(params.box_lo, dtype=float)
+    L = np.array(params.box, dtype=float)
+    q = np.floor((x - lo) / (L / nc)).astype(np.int64)
+    q = np.clip(q, 0, nc - 1)
+    counts = np.zeros(tuple(nc[::-1]), dtype=np.int64)       # [z, y, x]
+    np.add.at(counts, (q[:, 2], q[:, 1], q[:, 0]), 1)
+    neigh = np.zeros_like(counts)
+    for oz in (-1, 0, 1):
+        for oy in (-1, 0, 1):
+            for ox in (-1, 0, 1):
+                sh = counts
+                for axis, o, k in ((0, oz, 2), (1, oy, 1), (2, ox, 0)):
+                    if o == 0:
+                        continue
+                    if params.periodic[k]:
+                        sh = np.roll(sh, -o, axis=axis)
+                    else:
+                        pad = np.zeros_like(sh)
+                        idx = [slice(None)] * 3
+                        src = [slice(None)] * 3
+                        if o > 0:
+                            idx[axis] = slice(0, sh.shape[axis] - 1)
+                            src[axis] = slice(1, None)
+                        else:
+                            idx[axis] = slice(1, None)
+                            src[axis] = slice(0, sh.shape[axis] - 1)
+                        pad[tuple(idx)] = sh[tuple(src)]
+                        sh = pad
+                neigh += sh
+    return int((counts * neigh).sum())
 
 
 def dist_setup():
@@ -371,6 +420,22 @@ def run_ours(args):
 
     ms_max, value = aggregate_ranks(ms, n, K, world, device=dev)
 
+    # candidate tests of the density pass, counted from the state after the
+    # timed steps (rank 0; the other ranks hold replicas of the same workload)
+    cand = None
+    if rank == 0:
+        import numpy as np
+        xs = s.state()[0]
+        ws = w if args.workload == "batch" else [w]
+        off = 0
+        cand = 0
+        for wr in ws:
+            nr = wr.n if args.workload == "batch" else n
+            p = wr.params
+            ncell = [max(1, int(math.floor(p.box[k] / p.rc))) for k in range(3)]
+            cand += candidate_tests(xs[off:off + nr], p, ncell)
+            off += nr
+
     # end-to-end through the host-pointer C ABI: per step upload x, v from
     # pinned host memory, one step, read x, v back into pinned host memory
     e2e = None
@@ -402,14 +467,35 @@ def run_ours(args):
         peaks = measured_peaks()
         clk_mhz = peaks.get("sm_max_mhz", 2070.0)
         alu_peak = NUM_SMS * ISSUE_LANES_PER_SM_CLK * clk_mhz * 1e6 / 1e12     # Tlane-op/s
-        force_ms = prof.get("force", 0.0) / max(prof_steps, 1)
-        achieved = (pairs * OPS_PER_PAIR) / (force_ms * 1e-3) / 1e12 if force_ms > 0 else None
-        # HBM view of the same kernel: algorithmic bytes per particle of the fused
-        # force pass (FP32 tiles 16+16+4 read, FP64 x, v read and written 96)
-        bytes_pp = (36 if prec == 1 else 68) + 96
+        per = max(prof_steps, 1)
+        dens_ms = prof.get("density", 0.0) / per
+        force_ms = prof.get("force", 0.0) / per
+        traffic = kernel_traffic(args.workload, args.precision)
         hbm_peak = peaks.get("hbm_gbs", 6790.0)
-        hbm_ach = n * bytes_pp / (force_ms * 1e-3) / 1e9 if force_ms > 0 else None
-        traffic = force_traffic(args.workload, args.precision)
+        # lists: 4 B per directed partner; FP32 tiles 16 B (FP64 32 B)
+        tile = 16 if prec == 1 else 32
+        npart = pairs / max(n, 1)
+        dens_name = "k_density_cell" if (tuned and tuned["chosen"] == "nlist") or \
+            args.kernels == "nlist" else "k_density_nl"
+
+        def entry(name, work, ms_k, bytes_pp, what):
+            if ms_k <= 0:
+                return None
+            ach = work / (ms_k * 1e-3) / 1e12
+            gbs = n * bytes_pp / (ms_k * 1e-3) / 1e9
+            return {"kernel": name, "what": what, "ms": ms_k, "achieved": ach,
+                    "frac": ach / alu_peak, "traffic": traffic.get(name),
+                    "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak,
+                            "bytes_per_particle": bytes_pp, "peak_of": "measured"}}
+        kern = {
+            "density": entry(dens_name, cand * OPS_PER_CANDIDATE, dens_ms,
+                             tile + 8 + tile // 4 + 4 * npart + 4,
+                             f"{cand} candidate tests x {OPS_PER_CANDIDATE} ops"),
+            "force": entry("k_force_nl", pairs * OPS_PER_PAIR, force_ms,
+                           (tile * 2 + tile // 4) + 4 * npart + 4 + 96,
+                           f"{pairs} directed pairs x {OPS_PER_PAIR} ops"),
+        }
+        dom = max((k for k in kern if kern[k]), key=lambda k: kern[k]["ms"], default=None)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
@@ -435,14 +521,12 @@ def run_ours(args):
                        "l2": "flushed between timed steps" if flush else "working set > L2",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "pair_evals_per_s": value * pairs / 2 / n,
-            "roofline": {"bound": "alu", "kernel": "force pass (k_force, fused VV)",
-                         "achieved": achieved, "peak": alu_peak, "unit": "Tlane-op/s",
-                         "frac": (achieved / alu_peak) if achieved else None,
-                         "peak_note": "152 SMs x 128 lanes x sm_max_mhz (recipe clocks)",
-                         "traffic": traffic,
-                         "hbm": {"achieved_gbs": hbm_ach, "peak_gbs": hbm_peak,
-                                 "frac": (hbm_ach / hbm_peak) if hbm_ach else None,
-                                 "bytes_per_particle": bytes_pp, "peak_of": "measured"}},
+            "roofline": ({"bound": "alu", "kernel": kern[dom]["kernel"], "pass": dom,
+                          "achieved": kern[dom]["achieved"], "peak": alu_peak,
+                          "unit": "Tlane-op/s", "frac": kern[dom]["frac"],
+                          "traffic": kern[dom]["traffic"], "work": kern[dom]["what"],
+                          "peak_note": "152 SMs x 128 lanes x sm_max_mhz (recipe clocks)",
+                          "hbm": kern[dom]["hbm"], "all": kern} if dom else None),
             "kernel_ms_per_step": {k: v / max(prof_steps, 1) for k, v in prof.items()},
             "gpu_launches": launches,
             "cpu_baseline": cpu,

@@ -295,7 +295,8 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
  * launches each, and keep the fastest of each.  The trajectory is not
  * advanced.  chosen (may be NULL, 2 ints) receives the density variant and
  * the lanes per particle; ms (may be NULL, 5 doubles) the mean time of each
- * density variant, then of the force pass at 1, 2, 4 lanes (-1: not tried).
+ * density variant in that order, then of the force pass at 1, 2, 4 lanes
+ * (-1: not tried).
  * Synchronises. */
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms);
 

@@ -421,8 +421,9 @@ int step_launches(const mdpd_handle* h)
 
 void enqueue_density(mdpd_handle* h)
 {
+    const bool cell = h->kernels == MDPD_KERNELS_NLIST;
     if (h->nrep) {
-        if (h->kernels == MDPD_KERNELS_NLIST)
+        if (cell)
             launch_density_cell_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
                                       h->start, h->rho, h->nl, h->nl_count);
         else
@@ -434,9 +435,9 @@ void enqueue_density(mdpd_handle* h)
     if (h->want_phi)              // the wall density is accumulated by this variant only
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
                           h->cell_s, h->start, h->rho, h->nl, h->nl_count);
-    else if (h->kernels == MDPD_KERNELS_NLIST)
-        launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph,
-                            h->pos4, h->start, h->rho, h->nl, h->nl_count);
+    else if (cell)
+        launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph, h->pos4,
+                            h->start, h->rho, h->nl, h->nl_count);
     else if (h->kernels == MDPD_KERNELS_NLIST_THREAD)
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
                           h->cell_s, h->start, h->rho, h->nl, h->nl_count);

@@ -1,0 +1,363 @@
+// Density pass that also records each mobile particle's force partners
+// (arXiv:1903.10134, Sec. 2.1, Algorithm 1 step 4).
+//
+// Why lists: in a one-thread-per-particle scan of the 27 neighbour cells only
+// about 15 % of the candidates lie within r_c, so a force pass scanning cells
+// would execute the ~100 operations of a pair force for nearly every
+// candidate with most lanes idle.  The density pass already computes every
+// candidate distance; it records the candidates within r_c, and the force
+// pass (k_force.cu) runs the pair force only for real partners.  A list entry
+// is (j << 5) | image code, where the code (0..26) names the neighbour cell
+// offset (ox, oy, oz) that fixes the periodic image of j; so j < 2^27.
+// Lists are slot-major (nl[k * cap + i]) so consecutive particles store
+// consecutive words.  Particles with more than NL_MAX partners keep only the
+// count, and the force pass scans their cells directly.
+#include "pair.cuh"
+
+namespace mdpd {
+
+namespace {
+
+__device__ __forceinline__ int image_code(int ox, int oy, int oz)
+{
+    return (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
+}
+
+// Thread-per-particle variant: each thread scans its 27 neighbour cells and
+// stores its partners straight to the slot-major list (no shared-memory
+// staging, so occupancy is set by registers alone).  The density term is
+// evaluated under a branch: on the large porous systems this variant is picked
+// for, most warps have no candidate within r_d in an iteration, and a
+// branch-free weight (a reciprocal square root per candidate) measured slower.
+template <typename T, bool BATCH, bool WANT_PHI>
+__global__ void __launch_bounds__(PAIR_BLOCK, 12)
+k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
+             const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
+             const uint32_t* __restrict__ start, T* __restrict__ rho_out,
+             uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
+{
+    pdl_enter();
+    int s;
+    bool valid;
+    int64_t cell0 = 0;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        s = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        s = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = s < n;
+    }
+    if (!valid) return;
+    const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph = BATCH ? rp->ph : ph_p;
+    const Derived<T>& dc = derived<T>(ph);
+    const T rd2 = dc.rd2, rc2 = dc.rc2;
+    const T inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
+    const auto pi = pos4[s];
+    const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
+    const bool mobile = ph.list_all || mob_true;
+    // wall density of a mobile particle (WANT_PHI): sum over frozen partners
+    // within r_c of 15/(2 pi r_c^3) (1 - r/r_c)^2
+    const bool want_phi = WANT_PHI && mob_true;
+    const T inv_rc = dc.inv_rc;
+    const T cphi = dc.cw_phi;
+    T phi = T(0);
+    int q0, q1, q2;
+    cell_coords(cell_s[s], geo, q0, q1, q2);
+    T acc = ph.rho_self ? cw : T(0);
+    uint32_t cnt = 0;
+    for (int oz = -1; oz <= 1; ++oz) {
+        const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
+        if (z < 0) continue;
+        const T sz = pi.z - (T)oz * dc.h[2];
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
+            if (y < 0) continue;
+            const T sy = pi.y - (T)oy * dc.h[1];
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
+                if (x < 0) continue;
+                const T sx = pi.x - (T)ox * dc.h[0];
+                const uint32_t code = (uint32_t)image_code(ox, oy, oz);
+                const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
+                const uint32_t b = start[nc], e = start[nc + 1];
+                // the common path is one distance test: r_d <= r_c, so the
+                // density term, the list append and the self check all sit
+                // inside the r < r_c branch (about 15 % of the candidates)
+#pragma unroll 2
+                for (uint32_t j = b; j < e; ++j) {
+                    const auto pj = pos4[j];
+                    const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2 && j != (uint32_t)s) {
+                        if (r2 < rd2) {        // r = 0 (a coincident particle) gives w(0)
+                            const T w = T(1) - sqrt0_t(r2) * inv_rd;
+                            acc += cw * w * w;
+                        }
+                        if (mobile && r2 > T(0)) {
+                            if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
+                            ++cnt;
+                            if (want_phi && ((ph.frozen >> unpack_u32(pj.w)) & 1u)) {
+                                const T wq = T(1) - sqrt_t(r2) * inv_rc;
+                                phi += cphi * wq * wq;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    rho_out[s] = acc;
+    nl_count[s] = cnt;
+    if (WANT_PHI) ((T*)ph.phi_out)[s] = phi;
+}
+
+// Warp-cooperative density pass: one warp per home cell.  The 27 neighbour
+// cells' particles form one candidate sequence (a warp prefix sum over the
+// cells' counts); each lane takes one candidate per round of 32 and tests it
+// against up to DC_GROUP home particles broadcast from shared memory, so all
+// lanes run the same trip count.  Density terms accumulate per lane and are
+// summed with a fixed shuffle tree; partners within r_c of mobile home
+// particles are appended by warp ballot to per-particle lists staged in
+// shared memory, then written slot-major (nl[k * cap + i]).
+constexpr int DC_WARPS = 4;
+constexpr int DC_GROUP = 8;
+
+// The work of one warp on home cell c (global index; cell0 = first cell of
+// its replica).  Shared memory is per warp (index w).
+template <typename T>
+__device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, const Geo& geo,
+                                                  const Phys& ph,
+                                                  const typename Vec4<T>::type* __restrict__ pos4,
+                                                  const uint32_t* __restrict__ start,
+                                                  T* __restrict__ rho_out, int64_t cap,
+                                                  uint32_t* __restrict__ nl,
+                                                  uint32_t* __restrict__ nl_count)
+{
+    using V = typename Vec4<T>::type;
+    __shared__ V hpos[DC_WARPS][DC_GROUP];
+    __shared__ uint32_t pre[DC_WARPS][28];
+    __shared__ uint32_t cbase[DC_WARPS][27];
+    __shared__ uint32_t ccnt[DC_WARPS][DC_GROUP];
+    __shared__ uint32_t lst[DC_WARPS][NL_MAX][DC_GROUP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t hb = start[c], he = start[c + 1];
+    if (hb == he) return;                         // whole warp: empty cell
+    int q0, q1, q2;
+    cell_coords((uint32_t)(c - cell0), geo, q0, q1, q2);
+    uint32_t cb = 0, cn = 0;
+    if (lane < 27) {
+        const int x = neighbour_index(q0, lane % 3 - 1, geo.nc[0], geo.periodic[0]);
+        const int y = neighbour_index(q1, (lane / 3) % 3 - 1, geo.nc[1], geo.periodic[1]);
+        const int z = neighbour_index(q2, lane / 9 - 1, geo.nc[2], geo.periodic[2]);
+        if (x >= 0 && y >= 0 && z >= 0) {
+            const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
+            cb = start[nc];
+            cn = start[nc + 1] - cb;
+        }
+    }
+    uint32_t inc = cn;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const uint32_t C = __shfl_sync(0xffffffffu, inc, 31);
+    if (lane < 27) {
+        pre[w][lane] = inc - cn;
+        cbase[w][lane] = cb;
+    }
+    if (lane == 27) pre[w][27] = C;
+    __syncwarp();
+
+    const Derived<T>& dc = derived<T>(ph);
+    const T rc2 = dc.rc2;
+    const T inv_rd = dc.inv_rd;
+    const T cw = dc.cw_rho;
+    const T hx = dc.h[0], hy = dc.h[1], hz = dc.h[2];
+    const unsigned lt = (1u << lane) - 1u;
+
+    // far-away stand-in for the candidate slots past the end of the last round:
+    // beyond r_c and r_d of every home particle, finite in FP32
+    const T far = T(1e15);
+    for (uint32_t g0 = hb; g0 < he; g0 += DC_GROUP) {
+        const int ng = (int)min((uint32_t)DC_GROUP, he - g0);
+        bool mob_l = false;
+        if (lane < ng) {
+            const V ph_i = pos4[g0 + lane];
+            hpos[w][lane] = ph_i;
+            mob_l = ph.list_all || ((ph.frozen >> unpack_u32(ph_i.w)) & 1u) == 0u;
+        }
+        // home particles that take partner lists (warp-uniform)
+        const unsigned mobmask = __ballot_sync(0xffffffffu, mob_l);
+        __syncwarp();
+        T acc[DC_GROUP];
+        uint32_t cnt[DC_GROUP];
+#pragma unroll
+        for (int i = 0; i < DC_GROUP; ++i) {
+            acc[i] = T(0);
+            cnt[i] = 0;
+        }
+        for (uint32_t t0 = 0; t0 < C; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const bool valid = t < C;
+            int lo = 0, hi = 27;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (pre[w][mid] <= t) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t j = valid ? cbase[w][lo] + (t - pre[w][lo]) : hb;
+            const V pj = pos4[j];
+            // the candidate in the home cell's frame (its image across the
+            // neighbour cell offset)
+            const T cx = valid ? pj.x + (T)(lo % 3 - 1) * hx : far;
+            const T cy = valid ? pj.y + (T)((lo / 3) % 3 - 1) * hy : far;
+            const T cz = valid ? pj.z + (T)(lo / 9 - 1) * hz : far;
+            const uint32_t entry = (j << 5) | (uint32_t)lo;
+#pragma unroll
+            for (int i = 0; i < DC_GROUP; ++i) {
+                if (i < ng) {
+                    const V pi = hpos[w][i];
+                    const T dx = pi.x - cx;
+                    const T dy = pi.y - cy;
+                    const T dz = pi.z - cz;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    // branch-free weight; the home particle's own r = 0 term is
+                    // removed after the loop
+                    const T wr = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
+                    acc[i] += cw * wr * wr;
+                    if ((mobmask >> i) & 1u) {
+                        const bool hc = r2 < rc2 && r2 > T(0);
+                        const unsigned m = __ballot_sync(0xffffffffu, hc);
+                        if (m) {
+                            const uint32_t slot = cnt[i] + (uint32_t)__popc(m & lt);
+                            if (hc && slot < (uint32_t)NL_MAX) lst[w][slot][i] = entry;
+                            cnt[i] += (uint32_t)__popc(m);
+                        }
+                    }
+                }
+            }
+        }
+        uint32_t maxc = 0;
+#pragma unroll
+        for (int i = 0; i < DC_GROUP; ++i) {
+            if (i < ng) {
+                T v = acc[i];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == 0) {
+                    rho_out[g0 + i] = v - (ph.rho_self ? T(0) : cw);
+                    nl_count[g0 + i] = cnt[i];
+                }
+                const uint32_t kept = cnt[i] < (uint32_t)NL_MAX ? cnt[i] : (uint32_t)NL_MAX;
+                if (lane == i) ccnt[w][i] = kept;
+                maxc = kept > maxc ? kept : maxc;
+            }
+        }
+        __syncwarp();
+        for (uint32_t e = lane; e < maxc * DC_GROUP; e += 32) {
+            const uint32_t slot = e / DC_GROUP, i = e % DC_GROUP;
+            if ((int)i < ng && slot < ccnt[w][i]) nl[(int64_t)slot * cap + g0 + i] = lst[w][slot][i];
+        }
+        __syncwarp();
+    }
+}
+
+// One warp per home cell (a block per cell chunk of a batch).  The loops let
+// a grid smaller than the lattice walk it; a persistent grid of 16 blocks per
+// SM measured no faster than one warp per cell on the porous rock, the batch
+// of slabs or the slab.
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(DC_WARPS * 32)
+k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
+               const typename Vec4<T>::type* __restrict__ pos4,
+               const uint32_t* __restrict__ start, T* __restrict__ rho_out,
+               uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
+{
+    pdl_enter();
+    static_assert(DC_WARPS == BATCH_CELL_CHUNK, "a cell chunk is one block");
+    const int w = threadIdx.x >> 5;
+    if constexpr (BATCH) {
+        for (int b = blockIdx.x; b < bt.ncchunk; b += gridDim.x) {
+            const int4 ch = bt.cchunks[b];
+            const Rep& rp = block_rep<REP_SCALARS>(bt.reps, ch.x);
+            if (w < ch.z)
+                density_cell_warp<T>((int64_t)ch.y + w, rp.cell0, rp.geo, rp.ph, pos4, start,
+                                     rho_out, cap, nl, nl_count);
+            __syncthreads();              // the record is overwritten by the next chunk
+        }
+    } else {
+        for (int64_t c = (int64_t)blockIdx.x * DC_WARPS + w; c < ncell;
+             c += (int64_t)gridDim.x * DC_WARPS)
+            density_cell_warp<T>(c, 0, geo_p, ph_p, pos4, start, rho_out, cap, nl, nl_count);
+    }
+}
+
+}  // namespace
+
+void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                       const Phys& ph, const void* pos4, const uint32_t* cell_s,
+                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count)
+{
+    if (n <= 0) return;
+    const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
+    const bool phi = ph.phi_out != nullptr;
+    if (precision == 0)
+        launch_pdl(phi ? k_density_nl<double, false, true> : k_density_nl<double, false, false>,
+                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const D4*)pos4,
+                   cell_s, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl(phi ? k_density_nl<float, false, true> : k_density_nl<float, false, false>,
+                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const float4*)pos4,
+                   cell_s, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                             const void* pos4, const uint32_t* cell_s, const uint32_t* start,
+                             void* rho, uint32_t* nl, uint32_t* nl_count)
+{
+    if (bt.nchunk <= 0) return;
+    const dim3 g(bt.nchunk), b(PAIR_BLOCK);
+    if (precision == 0)
+        launch_pdl_smem(k_density_nl<double, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const D4*)pos4, cell_s, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl_smem(k_density_nl<float, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const float4*)pos4, cell_s, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
+                         const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,
+                         void* rho, uint32_t* nl, uint32_t* nl_count)
+{
+    if (ncell <= 0) return;
+    const unsigned nb = (unsigned)((ncell + DC_WARPS - 1) / DC_WARPS);
+    if (precision == 0)
+        launch_pdl(k_density_cell<double, false>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap,
+                   geo, ph, Batch{}, (const D4*)pos4, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl(k_density_cell<float, false>, dim3(nb), dim3(DC_WARPS * 32), st, ncell, cap,
+                   geo, ph, Batch{}, (const float4*)pos4, start, (float*)rho, nl, nl_count);
+}
+
+void launch_density_cell_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
+                               const void* pos4, const uint32_t* start, void* rho, uint32_t* nl,
+                               uint32_t* nl_count)
+{
+    if (bt.ncchunk <= 0) return;
+    const dim3 g(bt.ncchunk), b(DC_WARPS * 32);
+    if (precision == 0)
+        launch_pdl_smem(k_density_cell<double, true>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const D4*)pos4, start, (double*)rho, nl, nl_count);
+    else
+        launch_pdl_smem(k_density_cell<float, true>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
+                        bt, (const float4*)pos4, start, (float*)rho, nl, nl_count);
+}
+
+}  // namespace mdpd

@@ -384,7 +384,8 @@ def mdpd_force_vjp_dev(h, abar_t, xbar_t=None, ubar_t=None, theta_bar_t=None):
 
 
 class Tuned(tuple):
-    """Result of mdpd_autotune: unpacks as (density variant, [ms per variant]);
+    """Result of mdpd_autotune: unpacks as (density variant, [ms of NLIST,
+    NLIST_THREAD]);
     .lanes is the force pass's lanes per particle, .force_ms its times at 1, 2,
     4 lanes (-1: not tried)."""
 

@@ -100,7 +100,8 @@ def test_batch_graph_direct_autotune_and_set_state(M):
     x0, v0, _, _ = b1.state()
     res = b1.autotune(3)
     chosen, ms = res
-    assert chosen in (M.KERNELS_NLIST, M.KERNELS_NLIST_THREAD) and len(ms) == 2
+    assert chosen in (M.KERNELS_NLIST, M.KERNELS_NLIST_THREAD)
+    assert len(ms) == 2
     assert res.lanes == 1 and res.force_ms[1:] == [-1.0, -1.0]
     x1, v1, _, _ = b1.state()
     assert np.array_equal(x0, x1) and np.array_equal(v0, v1)
