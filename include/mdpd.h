@@ -326,6 +326,14 @@ int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_
 int mdpd_density_noalloc(const mdpd_params* params, int64_t n, const double* pos,
                          double* rho, void* cuda_stream);
 
+/* Measured FP32 issue rate of the current device, the denominator of the ALU
+ * roofline that the density and force passes are reported against: a
+ * full-occupancy grid of independent fused multiply-add chains, best of 4
+ * timed launches (about 50 ms in all).  lane_ops_per_s receives FMA
+ * lane-operations per second (one per lane per instruction), best_ms (may be
+ * NULL) the best launch time.  Errors: INVALID_ARG (NULL output), CUDA. */
+int mdpd_measure_fma_peak(double* lane_ops_per_s, double* best_ms);
+
 void mdpd_destroy(mdpd_handle* h);
 
 /* Message of the last error on h (or of the last failed mdpd_create when h is

@@ -97,7 +97,7 @@ SYMBOLS = (
     "mdpd_describe", "mdpd_autotune", "mdpd_set_params", "mdpd_set_step",
     "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error", "mdpd_create_batch", "mdpd_num_replicas", "mdpd_batch_observables",
-    "mdpd_batch_set_params",
+    "mdpd_batch_set_params", "mdpd_measure_fma_peak",
 )
 
 
@@ -145,6 +145,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_num_replicas.argtypes = [P, C.POINTER(i32)]
     L.mdpd_batch_observables.argtypes = [P, P, i32, i32]
     L.mdpd_batch_set_params.argtypes = [P, P]
+    L.mdpd_measure_fma_peak.argtypes = [C.POINTER(d), C.POINTER(d)]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -413,6 +414,13 @@ def mdpd_density_noalloc(params, pos_t, rho_t, stream=None):
     n = int(pos_t.shape[0])
     _check(lib().mdpd_density_noalloc(C.byref(cp), n, _tptr(pos_t), _tptr(rho_t),
                                       _stream_ptr(stream)))
+
+
+def mdpd_measure_fma_peak():
+    """(FMA lane-operations per second, best launch ms) of the current device."""
+    rate, ms = C.c_double(), C.c_double()
+    _check(lib().mdpd_measure_fma_peak(C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
 
 
 def mdpd_destroy(h):

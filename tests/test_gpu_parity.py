@@ -375,3 +375,15 @@ def test_split_and_fused_steps_agree_bitwise(M, precision):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
     a.close()
     b.close()
+
+
+def test_fma_peak_is_plausible(M):
+    """The measured FP32 issue rate (the ALU roofline's denominator) lies
+    between half and 1.1 times the nominal 128 lanes per SM per clock at the
+    maximum SM clock of this part (2.07 GHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nominal = sms * 128 * 2.07e9
+    rate, ms = M.mdpd_measure_fma_peak()
+    assert ms > 0
+    assert 0.5 * nominal < rate < 1.1 * nominal, (rate, nominal)
