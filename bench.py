@@ -248,6 +248,52 @@ def candidate_tests(x, params, ncell) -> int:
     return int((counts * neigh).sum())
 
 
+OBS_NAMES = ("px", "py", "pz", "ke", "kT", "Wxx", "Wyy", "Wzz", "Wxy", "Wxz", "Wyz",
+             "sum_vx2", "sum_vy2", "sum_vz2")
+
+
+def precision_error(mdpd, s, w, workload):
+    """Error of the FP32 pair arithmetic against the FP64 path (itself pinned
+    to the FP64 oracle at 1e-12 by the tests) on the bench's final state: an
+    FP64 handle is built from the same particles (wall particles included as
+    their frozen type), step index and seed; both evaluate forces, densities
+    and observables once.  For a batch, replica 0."""
+    import numpy as np
+    x, v, t, _ = s.state()
+    step = mdpd.mdpd_step_count(s.h)
+    f32, rho32 = s.forces()
+    if workload == "batch":
+        w0 = w[0]
+        a, b = 0, w0.n
+        x, v, t, f32, rho32 = x[a:b], v[a:b], t[a:b], f32[a:b], rho32[a:b]
+        obs32 = s.observables()[0]
+        p, seed = w0.params, w0.seed
+    else:
+        obs32 = s.observables()
+        p, seed = w.params, w.seed
+    with mdpd.System(p.copy(precision=0), x, v, t, seed) as d:
+        mdpd.mdpd_set_step(d.h, step)
+        f64, rho64 = d.forces()
+        obs64 = d.observables()
+    fn = np.linalg.norm(f64, axis=1)
+    rms = float(np.sqrt(np.mean(fn ** 2)))
+    ferr = np.linalg.norm(f32 - f64, axis=1) / np.maximum(fn, rms)
+    rerr = np.abs(rho32 - rho64) / np.maximum(np.abs(rho64), max(float(np.mean(rho64)), 1e-30))
+    # momentum is a cancelling sum: its error is stated relative to sum |m v|
+    scale = {k: abs(obs64[k]) for k in range(14)}
+    for k in range(3):
+        scale[k] = float(np.abs(v[:, k]).sum())
+    obs_err = {OBS_NAMES[k]: float(abs(obs32[k] - obs64[k]) / max(scale[k], 1e-30))
+               for k in range(14)}
+    return {"vs": "FP64 pair arithmetic on the GPU (pinned to the FP64 oracle at 1e-12)",
+            "n": int(len(x)), "force_rel_max": float(ferr.max()),
+            "force_rel_rms": float(np.sqrt(np.mean(ferr ** 2))),
+            "density_rel_max": float(rerr.max()), "observables_rel": obs_err,
+            "note": "per particle |f32 - f64| / max(|f64|, rms f64) and |rho32 - rho64| / "
+                    "max(rho64, mean rho64); momentum relative to sum |v|; one force evaluation "
+                    "at the final state"}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -502,6 +548,9 @@ def run_ours(args):
                            f"{pairs} directed pairs x {OPS_PER_PAIR} ops"),
         }
         dom = max((k for k in kern if kern[k]), key=lambda k: kern[k]["ms"], default=None)
+        err = None
+        if prec == 1 and not args.no_error:
+            err = precision_error(mdpd, s, w, args.workload)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
@@ -536,6 +585,7 @@ def run_ours(args):
             "kernel_ms_per_step": {k: v / max(prof_steps, 1) for k, v in prof.items()},
             "gpu_launches": launches,
             "cpu_baseline": cpu,
+            "fp32_error": err,
             "e2e": e2e,
             "clocks": clk,
         }
@@ -557,6 +607,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true",
                     help="no per-kernel events in the timed region (no roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-error", action="store_true",
+                    help="skip the FP32-vs-FP64 error evaluation after the timed steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
