@@ -289,6 +289,14 @@ int mdpd_get_accel_dev(mdpd_handle* h, double* accel);
 int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
                        double* theta_bar);
 
+/* Vector-Jacobian product of the density pass alone (Sec. 2.1): xbar (device,
+ * N x 3, id order) = d(sum_i rhobar_i rho_i)/dx at the current positions, for
+ * rhobar (device, N doubles, id order); every particle's density counts,
+ * frozen ones included.  Used to differentiate a loss on the local densities.
+ * Not on a batch handle.  Errors: INVALID_ARG, TILE_OVERFLOW (more than 64
+ * partners within r_c), CUDA.  Synchronises. */
+int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar);
+
 /* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD)
  * and then the force pass at 1, 2 and 4 lanes per particle
  * (MDPD_OPT_FORCE_LANES; 1 only on a batch) on the current state, reps

@@ -103,6 +103,34 @@ class _Window(torch.autograd.Function):
         return xb, vb, tb[0], tb[1], tb[2], None, None, None, None
 
 
+class _Density(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, system):
+        zero = torch.zeros_like(x)
+        M.mdpd_set_state_dev(system.h, x.detach().contiguous(), zero)
+        rho = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+        M.mdpd_forces_dev(system.h, None, rho)
+        ctx.system = system
+        ctx.save_for_backward(x.detach())
+        return rho
+
+    @staticmethod
+    def backward(ctx, rbar):
+        (x,) = ctx.saved_tensors
+        M.mdpd_set_state_dev(ctx.system.h, x.contiguous(), torch.zeros_like(x))
+        xb = torch.empty_like(x)
+        M.mdpd_density_vjp_dev(ctx.system.h, rbar.double().contiguous(), xb)
+        return xb, None
+
+
+def density(system, x):
+    """Differentiable local densities rho_i (Sec. 2.1) of the system's particles
+    at positions x (N x 3, device): forward through the density pass, backward
+    through its vector-Jacobian product (mdpd_density_vjp_dev).  The system's
+    state is overwritten (positions x, velocities zero)."""
+    return _Density.apply(x, system)
+
+
 def window(system, params, x0, v0, A, B, gamma, nsteps: int, step0: int = 0):
     """Differentiable (x_K, v_K) after nsteps velocity-Verlet steps (see module)."""
     return _Window.apply(x0, v0, A, B, gamma, system, params, int(nsteps), int(step0))

@@ -1387,6 +1387,30 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
     return MDPD_OK;
 }
 
+int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
+    if (rc) return rc;
+    if (!rhobar || !xbar) return h->fail(MDPD_ERR_INVALID_ARG, "rhobar and xbar are required");
+    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "the density VJP is not available on a batch handle");
+    if ((rc = check_ptr_kind(h, rhobar, true)) || (rc = check_ptr_kind(h, xbar, true))) return rc;
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    h->ph.list_all = 1;                      // lists for every particle, frozen ones too
+    rc = evaluate(h, h->fout, true);
+    h->ph.list_all = 0;
+    if (rc) return rc;
+    const int c = h->cur;
+    double* xs = h->x[1 - c];                // scratch: [3][cap]; rbar [cap]
+    double* rs = h->a[1 - c];
+    launch_density_vjp(st, h->precision, n, h->cap, h->geo, h->ph, h->pos4, h->nl, h->nl_count,
+                       h->id[c], rhobar, rs, xs, h->status);
+    launch_scatter_by_id(st, n, h->cap, h->id[c], xs, xbar);
+    CK(cudaGetLastError());
+    return sync_check(h);
+}
+
 int mdpd_get_wall_density(mdpd_handle* h, double* phi)
 {
     if (!h || !phi) return MDPD_ERR_INVALID_ARG;

@@ -129,7 +129,8 @@ template <typename T>
 __global__ void __launch_bounds__(PAIR_BLOCK)
 k_density_vjp(int n, int64_t cap, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ pos4,
               const uint32_t* __restrict__ nl, const uint32_t* __restrict__ nl_count,
-              const double* __restrict__ rbar, double* __restrict__ xbar)
+              const double* __restrict__ rbar, double* __restrict__ xbar,
+              uint32_t* __restrict__ status)
 {
     using V = typename Vec4<T>::type;
     __shared__ T shift[27][3];
@@ -149,6 +150,7 @@ k_density_vjp(int n, int64_t cap, Geo geo, Phys ph, const typename Vec4<T>::type
     const T rb_i = (T)rbar[s];
     T g[3] = { T(0), T(0), T(0) };
     const uint32_t cnt = nl_count[s];
+    if (cnt > (uint32_t)NL_MAX) atomicOr(status, ST_OVERFLOW);
     const uint32_t m = cnt < (uint32_t)NL_MAX ? cnt : (uint32_t)NL_MAX;
     for (uint32_t k = 0; k < m; ++k) {
         const uint32_t e = nl[(int64_t)k * cap + s];
@@ -169,7 +171,32 @@ k_density_vjp(int n, int64_t cap, Geo geo, Phys ph, const typename Vec4<T>::type
     for (int c = 0; c < 3; ++c) xbar[c * cap + s] += (double)g[c];
 }
 
+// rbar in cell order from the caller's rhobar in id order.
+__global__ void k_gather_by_id(int n, const uint32_t* __restrict__ id,
+                               const double* __restrict__ in, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n) out[s] = in[id[s]];
+}
+
 }  // namespace
+
+void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                        const Phys& ph, const void* pos4, const uint32_t* nl,
+                        const uint32_t* nl_count, const uint32_t* id, const double* rhobar,
+                        double* rbar, double* xbar, uint32_t* status)
+{
+    if (n <= 0) return;
+    const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
+    k_gather_by_id<<<nb, PAIR_BLOCK, 0, st>>>(n, id, rhobar, rbar);
+    cudaMemsetAsync(xbar, 0, 3 * (size_t)cap * sizeof(double), st);
+    if (precision == 0)
+        k_density_vjp<double><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const D4*)pos4, nl,
+                                                         nl_count, rbar, xbar, status);
+    else
+        k_density_vjp<float><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const float4*)pos4, nl,
+                                                        nl_count, rbar, xbar, status);
+}
 
 void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                       const Phys& ph, const void* pos4, const void* vel4, const void* rho,
@@ -185,14 +212,14 @@ void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const 
                                                        nl_count, step_ptr, abar, xbar, ubar, rbar,
                                                        tbar, status);
         k_density_vjp<double><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const D4*)pos4, nl,
-                                                         nl_count, rbar, xbar);
+                                                         nl_count, rbar, xbar, status);
     } else {
         k_force_vjp<float><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const float4*)pos4,
                                                       (const float4*)vel4, (const float*)rho, nl,
                                                       nl_count, step_ptr, abar, xbar, ubar, rbar,
                                                       tbar, status);
         k_density_vjp<float><<<nb, PAIR_BLOCK, 0, st>>>(n, cap, geo, ph, (const float4*)pos4, nl,
-                                                        nl_count, rbar, xbar);
+                                                        nl_count, rbar, xbar, status);
     }
 }
 

@@ -307,6 +307,13 @@ void launch_reduce_obs_batch(cudaStream_t st, int precision, const double* parti
 // VJP of one force evaluation at the current cell-ordered state (lists built
 // with list_all); xbar, ubar component-major [3][cap], rbar [cap] scratch,
 // tbar [3][64] accumulated with atomics (zero it first).
+// VJP of the density pass alone: xbar (component-major [3][cap], zeroed here)
+// = d(sum_i rhobar_i rho_i)/dx for rhobar given in id order (rbar: [cap]
+// scratch), over the lists of the last density pass (built with list_all).
+void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                        const Phys& ph, const void* pos4, const uint32_t* nl,
+                        const uint32_t* nl_count, const uint32_t* id, const double* rhobar,
+                        double* rbar, double* xbar, uint32_t* status);
 void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                       const Phys& ph, const void* pos4, const void* vel4, const void* rho,
                       const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,

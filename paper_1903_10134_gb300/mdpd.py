@@ -97,7 +97,7 @@ SYMBOLS = (
     "mdpd_describe", "mdpd_autotune", "mdpd_set_params", "mdpd_set_step",
     "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error", "mdpd_create_batch", "mdpd_num_replicas", "mdpd_batch_observables",
-    "mdpd_batch_set_params", "mdpd_measure_fma_peak",
+    "mdpd_batch_set_params", "mdpd_measure_fma_peak", "mdpd_density_vjp_dev",
 )
 
 
@@ -146,6 +146,7 @@ def lib(build_if_stale: bool = True):
     L.mdpd_batch_observables.argtypes = [P, P, i32, i32]
     L.mdpd_batch_set_params.argtypes = [P, P]
     L.mdpd_measure_fma_peak.argtypes = [C.POINTER(d), C.POINTER(d)]
+    L.mdpd_density_vjp_dev.argtypes = [P, P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -356,6 +357,10 @@ def mdpd_describe(h):
     lps = C.c_int32()
     _check(lib().mdpd_describe(h, _p(nc), C.byref(lps)), h)
     return nc.tolist(), int(lps.value)
+
+
+def mdpd_density_vjp_dev(h, rhobar_t, xbar_t):
+    _check(lib().mdpd_density_vjp_dev(h, _tptr(rhobar_t), _tptr(xbar_t)), h)
 
 
 def mdpd_get_wall_density(h) -> np.ndarray:

@@ -146,3 +146,75 @@ def test_fit_A_B_from_a_target_window(env):
     a, b = theta.detach().cpu().numpy()
     assert abs(a - (-40.0)) < 1e-3 * 40 and abs(b - 25.0) < 1e-3 * 25, (a, b)
     s.close()
+
+
+def _oracle_density_loss(w, p, x, rb):
+    o = O.Oracle(p, x, w.vel, w.type, w.seed, use_cells=True)
+    return float(np.sum(rb * o.density()))
+
+
+@pytest.mark.parametrize("frozen", [(), (1,)])
+def test_density_vjp_matches_oracle_finite_differences(env, frozen):
+    """d(sum_i rhobar_i rho_i)/dx from the density pass's VJP kernel against
+    central differences of the oracle's densities (FP64; w_rho is C1 at r_d,
+    so the differences have no kink)."""
+    torch, M, AD = env
+    w = I.tiny(900, (5.0, 5.5, 4.5), 23, ntypes=2, frozen_types=frozen)
+    p = w.params.copy(precision=0)
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    rng = np.random.default_rng(5)
+    rb = rng.normal(size=w.n)
+    x = torch.tensor(w.pos, device="cuda")
+    xt = x.clone().requires_grad_(True)
+    rho = AD.density(s, xt)
+    assert np.allclose(rho.detach().cpu().numpy(),
+                       O.Oracle(p, w.pos, w.vel, w.type, w.seed).density(), rtol=1e-13, atol=1e-13)
+    (rho * torch.tensor(rb, device="cuda")).sum().backward()
+    g = xt.grad.cpu().numpy()
+    eps = 1e-6
+    for _ in range(3):
+        d = rng.normal(size=w.pos.shape)
+        fd = (_oracle_density_loss(w, p, w.pos + eps * d, rb) -
+              _oracle_density_loss(w, p, w.pos - eps * d, rb)) / (2 * eps)
+        assert abs(fd - np.sum(g * d)) <= 1e-6 * max(1.0, abs(fd)), (fd, np.sum(g * d))
+    s.close()
+
+
+def test_fit_A_to_a_target_local_density(env):
+    """Calibration through the window and the density VJP: the mean local
+    density after a 10-step window of a bulk box is the target made with
+    A = -40 (B fixed at 25); gradient descent on A from -30 on
+    (mean rho(x_K) - target)^2 approaches -40."""
+    torch, M, AD = env
+    w = I.tiny(700, (5.0, 5.0, 5.0), 41)
+    p = w.params.copy(precision=0)
+    s = M.System(p, w.pos, w.vel, w.type, w.seed)
+    dev = "cuda"
+    x0 = torch.tensor(w.pos, device=dev)
+    v0 = torch.tensor(w.vel, device=dev)
+    ones = torch.ones((8, 8), dtype=torch.float64, device=dev)
+    B = torch.tensor(p.B, device=dev)
+    G = torch.tensor(p.gamma, device=dev)
+    K = 10
+    with torch.no_grad():
+        xt, _ = AD.window(s, p, x0, v0, -40.0 * ones, B, G, K)
+    target = float(AD.density(s, xt).mean())
+
+    def loss_and_grad(a):
+        A = torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=True)
+        xk, _ = AD.window(s, p, x0, v0, A * ones, B, G, K)
+        loss = (AD.density(s, xk).mean() - target) ** 2
+        loss.backward()
+        return float(loss.detach()), float(A.grad)
+
+    a = -30.0
+    l0, _ = loss_and_grad(a)
+    for _ in range(12):
+        l, g = loss_and_grad(a)
+        # Newton-like step on the scalar quadratic model l = (m(a) - t)^2
+        step = 2.0 * l / g if g != 0 else 0.0
+        a -= float(np.clip(step, -5.0, 5.0))
+    lf, _ = loss_and_grad(a)
+    assert lf < 1e-3 * l0, (l0, lf, a)
+    assert abs(a - (-40.0)) < 0.5, a
+    s.close()
