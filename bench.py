@@ -252,6 +252,57 @@ OBS_NAMES = ("px", "py", "pz", "ke", "kT", "Wxx", "Wyy", "Wzz", "Wxy", "Wxz", "W
              "sum_vx2", "sum_vy2", "sum_vz2")
 
 
+def fp64_leg(mdpd, args, stream, pairs32):
+    """The same workload with FP64 pair arithmetic: autotuned, warmed up, then
+    min(K, 100) steps timed with CUDA events (same L2 rule as the FP32 run)."""
+    import torch
+    w = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
+    if args.workload == "batch":
+        s = mdpd.Batch.from_workloads(w, stream=stream)
+    else:
+        s = mdpd.System.from_workload(w, stream=stream)
+    try:
+        s.autotune()
+        for _ in range(3):
+            s.step(1)
+        s.sync()
+        n = s.n
+        K = max(3, min(args.steps, 100))
+        working_set = n * (32 + 32 + 8 + 4 + 2 * 3 * 24 + 8)
+        flush = working_set < 4 * L2_BYTES
+        flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32,
+                                device=torch.cuda.current_device()) if flush else None
+        torch.cuda.synchronize()
+        if flush:
+            ms = 0.0
+            for _ in range(K):
+                with torch.cuda.stream(stream):
+                    flush_buf.fill_(1.0)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                s.step(1)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms += a.elapsed_time(b)
+        else:
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(K)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+        s.sync()
+        pairs = s.pair_count()
+        value = n * K / (ms * 1e-3)
+        return {"value": value, "unit": "particle-steps/s", "ms_per_step": ms / K, "steps": K,
+                "pair_evals_per_s": value * pairs / 2 / n, "dtype": "f64",
+                "l2": "flushed between timed steps" if flush else "working set > L2"}
+    finally:
+        s.close()
+
+
 def precision_error(mdpd, s, w, workload):
     """Error of the FP32 pair arithmetic against the FP64 path (itself pinned
     to the FP64 oracle at 1e-12 by the tests) on the bench's final state: an
@@ -548,6 +599,9 @@ def run_ours(args):
                            f"{pairs} directed pairs x {OPS_PER_PAIR} ops"),
         }
         dom = max((k for k in kern if kern[k]), key=lambda k: kern[k]["ms"], default=None)
+        fp64 = None
+        if prec == 1 and not args.no_fp64:
+            fp64 = fp64_leg(mdpd, args, stream, pairs)
         err = None
         if prec == 1 and not args.no_error:
             err = precision_error(mdpd, s, w, args.workload)
@@ -564,6 +618,30 @@ def run_ours(args):
                           f"workload (N={info['n']}), {info['seconds']:.1f} s")
             cpu = {"value": info["value"], "unit": "particle-steps/s", "cores": info["cores"],
                    "kind": "oracle", "sample": sample}
+            # the same oracle on one thread (its sums do not depend on the thread
+            # count), when one step of it fits the budget: estimated from the
+            # all-thread step time
+            from oracle import oracle as O
+            nthr = O.num_threads()
+            per_step = info["seconds"] / max(info["steps"], 1)
+            if args.workload == "batch" or per_step * nthr <= args.cpu_seconds / 3:
+                O.set_num_threads(1)
+                try:
+                    wc1 = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
+                    if args.workload == "batch":
+                        i1 = oracle_throughput_batch(wc1, args.cpu_seconds / 3)
+                        s1 = f"one step of each of the first {i1['replicas']} replicas"
+                    else:
+                        i1 = oracle_throughput(wc1, args.cpu_seconds / 3, max_steps=200)
+                        s1 = f"{i1['steps']} steps of the full workload"
+                finally:
+                    O.set_num_threads(nthr)
+                cpu["one_thread"] = {"value": i1["value"], "cores": 1,
+                                     "sample": f"{s1}, {i1['seconds']:.1f} s"}
+            else:
+                cpu["one_thread"] = {"value": None, "cores": 1,
+                                     "sample": f"skipped: one step takes about "
+                                               f"{per_step * nthr:.0f} s on one thread"}
         line = {
             "metric": "particle-steps/s", "value": value, "unit": "particle-steps/s",
             "n_gpus": world, "steps": K, "warmup": args.warmup,
@@ -586,6 +664,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "fp32_error": err,
+            "fp64": fp64,
             "e2e": e2e,
             "clocks": clk,
         }
@@ -607,6 +686,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true",
                     help="no per-kernel events in the timed region (no roofline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 throughput leg after the FP32 run")
     ap.add_argument("--no-error", action="store_true",
                     help="skip the FP32-vs-FP64 error evaluation after the timed steps")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -584,6 +584,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads used by later calls (n >= 1); the sums are gather-only, so results */
+/* do not depend on it.                                                        */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* Forces on a subset of particles (indices idx[0..m-1]) of the whole system,  */
 /* with rho given for every particle; same definition as orc_forces.          */
 int orc_forces_subset(const orc_sys *s, int64_t n, const double *x, const double *v,

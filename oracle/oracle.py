@@ -68,6 +68,8 @@ def lib():
         _lib.orc_place_walls.argtypes = [P, P, P, d, P, d, d, u64, P, i64, P]
         _lib.orc_place_walls.restype = i64
         _lib.orc_num_threads.restype = C.c_int
+        _lib.orc_set_num_threads.argtypes = [C.c_int]
+        _lib.orc_set_num_threads.restype = None
         _lib.orc_forces_subset.argtypes = [P, i64, P, P, P, P, P, u64, i64, P, P]
         _lib.orc_force_vjp.argtypes = [P, i64, P, P, P, P, u64, P, P, P, P]
     return _lib
@@ -163,6 +165,11 @@ def place_walls(mask, periodic, voxel: float, origin, rho_w: float, shell: float
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of later oracle calls (results do not depend on it)."""
+    lib().orc_set_num_threads(int(n))
 
 
 class Oracle:

@@ -82,6 +82,7 @@ struct mdpd_handle {
     // graphs[profiled][mode: 0 fused, 1 last][cur][first half-kick in the binning]
     bool use_graph = true;
     Graphs g[2][2][2][2];
+    Graphs gm[2];                    // MULTI_STEPS fused steps in one graph, by cur
     cudaEvent_t tev[EV_PER_STEP] = {};
 
     // profiling ring
@@ -253,6 +254,11 @@ void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
 
 void destroy_graphs(mdpd_handle* h)
 {
+    for (auto& gg : h->gm) {
+        if (gg.exec) cudaGraphExecDestroy(gg.exec);
+        if (gg.graph) cudaGraphDestroy(gg.graph);
+        gg = Graphs();
+    }
     for (auto& a : h->g)
         for (auto& b : a)
             for (auto& c : b)
@@ -503,6 +509,33 @@ int evaluate(mdpd_handle* h, double* out, bool keep_a)
     enqueue_force(h, FM_EVAL, 0, out ? out : h->a[h->cur]);
     enqueue_reduce(h, 0);
     CK(cudaGetLastError());
+    return MDPD_OK;
+}
+
+// Fused steps captured together (even, so the buffer parity returns to the
+// starting one): the time-step loop runs as one graph launch per MULTI_STEPS
+// steps when no per-step profiling events are pending.
+constexpr int MULTI_STEPS = 8;
+
+int capture_multi(mdpd_handle* h, int cur)
+{
+    Graphs& gg = h->gm[cur];
+    const int saved = h->cur;
+    h->cur = cur;
+    CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < MULTI_STEPS; ++k) enqueue_step(h, FM_FUSED, false, nullptr);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
+    h->cur = saved;
+    if (e != cudaSuccess) return h->fail(MDPD_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return h->fail(MDPD_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    gg.graph = graph;
+    gg.exec = exec;
     return MDPD_OK;
 }
 
@@ -1042,6 +1075,18 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     // the first step's binning applies the first half-kick and drift; later
     // steps get them from the previous force pass (FM_FUSED)
     for (int64_t k = 0; k < nsteps; ++k) {
+        const bool middle = k > 0 && k + MULTI_STEPS < nsteps;    // fused, no kick
+        if (middle && h->use_graph && h->prof_used >= h->prof_cap) {
+            Graphs& gg = h->gm[h->cur];
+            if (!gg.exec) {
+                int rc = capture_multi(h, h->cur);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(gg.exec, h->stream));
+            h->prof_launches += (int64_t)MULTI_STEPS * step_launches(h);
+            k += MULTI_STEPS - 1;              // the parity is unchanged (even count)
+            continue;
+        }
         int rc = run_step(h, k + 1 < nsteps ? FM_FUSED : FM_LAST, k == 0);
         if (rc) return rc;
     }

@@ -387,3 +387,24 @@ def test_fma_peak_is_plausible(M):
     rate, ms = M.mdpd_measure_fma_peak()
     assert ms > 0
     assert 0.5 * nominal < rate < 1.1 * nominal, (rate, nominal)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_step_graph_matches_direct_launches(M, precision):
+    """step(37) replays 8-step graphs for the middle of the call; the
+    trajectory equals direct launches bit for bit, and the launch count is
+    unchanged."""
+    w = I.tiny(2500, (7.0, 7.5, 6.5), 29, ntypes=2)
+    a, _ = make(M, w, precision)
+    b, _ = make(M, w, precision)
+    b.set_option(M.OPT_GRAPH, 0)
+    for s in (a, b):
+        s.set_option(M.OPT_PROFILE, 0)
+        s.step(37)
+        s.step(11)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    assert np.array_equal(a.observables(), b.observables())
+    a.close()
+    b.close()

@@ -273,3 +273,20 @@ def test_wall_particles_inside_shell_and_density():
     assert abs(len(pos) - expect) < 4 * math.sqrt(0.25 * sh.sum()) + 1
     pos2, _ = O.place_walls(mask, (1, 1, 1), voxel, (0.0, 0.0, 0.0), rho_w, 1.0, 77)
     assert np.array_equal(pos, pos2)
+
+
+def test_oracle_results_do_not_depend_on_thread_count():
+    """Gather-only sums: densities, forces and a few steps are bit-identical
+    with one thread and with all threads."""
+    w = I.tiny(800, (5.0, 5.0, 5.0), 13, ntypes=2)
+    n0 = O.num_threads()
+    out = []
+    for t in (1, n0):
+        O.set_num_threads(t)
+        o = O.Oracle(w.params, w.pos, w.vel, w.type, w.seed, use_cells=True)
+        a, _ = o.forces()
+        o.run(3)
+        out.append((o.density(), a, o.x.copy()))
+    O.set_num_threads(n0)
+    for u, v in zip(*out):
+        assert np.array_equal(u, v)
