@@ -185,6 +185,20 @@ int mdpd_set_state(mdpd_handle* h, const double* pos, const double* vel);
 /* Device-array variant of mdpd_set_state. */
 int mdpd_set_state_dev(mdpd_handle* h, const double* pos, const double* vel);
 
+/* Checkpoint and bit-exact resume.  mdpd_get_accel (host, N x 3, id order)
+ * returns the accelerations the next step's first half-kick will use: those
+ * of the last force evaluation, a(t + dt) computed with the half-step
+ * velocity.  mdpd_set_state_accel loads positions, velocities and those
+ * accelerations without evaluating the forces, so a run resumed from
+ * (mdpd_get_state, mdpd_get_accel, mdpd_step_count, seed) with mdpd_create,
+ * mdpd_set_step and mdpd_set_state_accel continues bit for bit (Philox is
+ * keyed on the step, not on a running state).  Until the next step or force
+ * evaluation the densities returned by mdpd_get_state are stale.
+ * Errors: INVALID_ARG, NONFINITE, CUDA.  Synchronise. */
+int mdpd_get_accel(mdpd_handle* h, double* accel);
+int mdpd_set_state_accel(mdpd_handle* h, const double* pos, const double* vel,
+                         const double* accel);
+
 /* Evaluate, without stepping, the density and the forces at the current
  * positions and velocities with the current step index: force gets 3N doubles
  * (sum_j F_ij + g for mobile particles, m = 1; 0 for frozen ones), rho N

@@ -715,10 +715,10 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
     }
     h->cur = 0;
     if (h->nrep)
-        launch_load_state_batch(st, h->cap, h->fout, h->x[1], h->batch(), master(h, 0),
+        launch_load_state_batch(st, h->cap, h->fout, h->x[1], nullptr, h->batch(), master(h, 0),
                                 h->type_by_id, h->status);
     else
-        launch_load_state(st, (int)n, h->cap, h->fout, h->x[1], h->geo, master(h, 0),
+        launch_load_state(st, (int)n, h->cap, h->fout, h->x[1], nullptr, h->geo, master(h, 0),
                           h->type_by_id, h->status);
     if ((rc = evaluate(h, nullptr, false))) return bail(rc);
     if ((rc = sync_check(h))) return bail(rc);
@@ -1163,7 +1163,10 @@ int mdpd_get_state_dev(mdpd_handle* h, double* pos, double* vel, int32_t* type, 
     return get_state_impl(h, pos, vel, type, rho, true);
 }
 
-static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, bool dev)
+// acc (may be NULL): accelerations to restore instead of evaluating the
+// forces at the loaded state (a checkpoint of a run resumes bit for bit).
+static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, const double* acc,
+                          bool dev)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (h->n > 0 && (!pos || !vel)) return h->fail(MDPD_ERR_INVALID_ARG, "pos and vel are required");
@@ -1175,32 +1178,58 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
     const int c = h->cur;
     const double* d_pos = pos;
     const double* d_vel = vel;
+    const double* d_acc = nullptr;
     if (!dev && n > 0) {
         CK(cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(h->x[1 - c], vel, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
         d_pos = h->fout;
         d_vel = h->x[1 - c];
+        if (acc) {
+            CK(cudaMemcpyAsync(h->v[1 - c], acc, (size_t)n * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+            d_acc = h->v[1 - c];
+        }
     }
     if (h->nrep)
-        launch_load_state_batch(st, h->cap, d_pos, d_vel, h->batch(), master(h, c), h->type_by_id,
-                                h->status);
+        launch_load_state_batch(st, h->cap, d_pos, d_vel, d_acc, h->batch(), master(h, c),
+                                h->type_by_id, h->status);
     else
-        launch_load_state(st, n, h->cap, d_pos, d_vel, h->geo, master(h, c), h->type_by_id,
+        launch_load_state(st, n, h->cap, d_pos, d_vel, d_acc, h->geo, master(h, c), h->type_by_id,
                           h->status);
+    if (acc) {
+        CK(cudaGetLastError());
+        return MDPD_OK;
+    }
     if ((rc = evaluate(h, nullptr, false))) return rc;
     return MDPD_OK;
 }
 
 int mdpd_set_state(mdpd_handle* h, const double* pos, const double* vel)
 {
-    int rc = set_state_impl(h, pos, vel, false);
+    return set_state_impl(h, pos, vel, nullptr, false);
+}
+
+int mdpd_set_state_accel(mdpd_handle* h, const double* pos, const double* vel, const double* accel)
+{
+    if (h && h->n > 0 && !accel) return h->fail(MDPD_ERR_INVALID_ARG, "accel is required");
+    return set_state_impl(h, pos, vel, accel, false);
+}
+
+int mdpd_get_accel(mdpd_handle* h, double* accel)
+{
+    if (!h || !accel) return MDPD_ERR_INVALID_ARG;
+    int rc = sync_check(h);
     if (rc) return rc;
-    return MDPD_OK;
+    double* tmp = h->x[1 - h->cur];
+    launch_scatter_by_id(h->stream, (int)h->n, h->cap, h->id[h->cur], h->a[h->cur], tmp);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(accel, tmp, (size_t)h->n * 3 * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
+    return sync_check(h);
 }
 
 int mdpd_set_state_dev(mdpd_handle* h, const double* pos, const double* vel)
 {
-    return set_state_impl(h, pos, vel, true);
+    return set_state_impl(h, pos, vel, nullptr, true);
 }
 
 static int forces_impl(mdpd_handle* h, double* force, double* rho, bool dev)

@@ -266,7 +266,8 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
 // arrays (index = id), wrapping periodic axes.
 template <bool BATCH>
 __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3,
-                             const double* __restrict__ vel3, Geo geo_p, Batch bt, Master m,
+                             const double* __restrict__ vel3, const double* __restrict__ acc3,
+                             Geo geo_p, Batch bt, Master m,
                              const uint8_t* __restrict__ type_by_id, uint32_t* __restrict__ status)
 {
     pdl_enter();
@@ -297,7 +298,7 @@ __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3
         }
         m.x[k * cap + i] = x;
         m.v[k * cap + i] = v;
-        m.a[k * cap + i] = 0.0;
+        m.a[k * cap + i] = acc3 ? acc3[3 * i + k] : 0.0;
     }
     if (st) atomicOr(status, st);
     m.id[i] = (uint32_t)i;
@@ -415,21 +416,21 @@ void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
-                       const double* vel3, const Geo& geo, const Master& m,
+                       const double* vel3, const double* acc3, const Geo& geo, const Master& m,
                        const uint8_t* type_by_id, uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_load_state<false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, pos3, vel3, geo,
-               Batch{}, m, type_by_id, status);
+    launch_pdl(k_load_state<false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, pos3, vel3, acc3,
+               geo, Batch{}, m, type_by_id, status);
 }
 
 void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, const double* vel3,
-                             const Batch& bt, const Master& m, const uint8_t* type_by_id,
-                             uint32_t* status)
+                             const double* acc3, const Batch& bt, const Master& m,
+                             const uint8_t* type_by_id, uint32_t* status)
 {
     if (bt.nchunk <= 0) return;
     launch_pdl_smem(k_load_state<true>, dim3(bt.nchunk), dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap,
-                    pos3, vel3, Geo{}, bt, m, type_by_id, status);
+                    pos3, vel3, acc3, Geo{}, bt, m, type_by_id, status);
 }
 
 void launch_scatter_by_id(cudaStream_t st, int n, int64_t cap, const uint32_t* id,

@@ -281,8 +281,8 @@ void launch_reduce_obs(cudaStream_t st, int precision, const double* partials, i
 // ---- launchers (batch of replicas; see Batch) ------------------------------
 constexpr int OBS_STRIDE = 2 * MDPD_NUM_OBS + 2;   // per-replica observable record
 void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, const double* vel3,
-                             const Batch& bt, const Master& m, const uint8_t* type_by_id,
-                             uint32_t* status);
+                             const double* acc3, const Batch& bt, const Master& m,
+                             const uint8_t* type_by_id, uint32_t* status);
 void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
                             bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
                             uint32_t* status);
@@ -337,8 +337,10 @@ void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const ui
                                  const void* rho_sorted, double* out);
 void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const uint8_t* type,
                                int32_t* out);
+// Master state in id order from pos3, vel3 and (if not NULL) acc3, all
+// interleaved xyz; periodic axes wrapped.
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
-                       const double* vel3, const Geo& geo, const Master& m,
+                       const double* vel3, const double* acc3, const Geo& geo, const Master& m,
                        const uint8_t* type_by_id, uint32_t* status);
 
 }  // namespace mdpd

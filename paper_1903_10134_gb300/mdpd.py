@@ -98,6 +98,7 @@ SYMBOLS = (
     "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error", "mdpd_create_batch", "mdpd_num_replicas", "mdpd_batch_observables",
     "mdpd_batch_set_params", "mdpd_measure_fma_peak", "mdpd_density_vjp_dev",
+    "mdpd_get_accel", "mdpd_set_state_accel",
 )
 
 
@@ -147,6 +148,8 @@ def lib(build_if_stale: bool = True):
     L.mdpd_batch_set_params.argtypes = [P, P]
     L.mdpd_measure_fma_peak.argtypes = [C.POINTER(d), C.POINTER(d)]
     L.mdpd_density_vjp_dev.argtypes = [P, P, P]
+    L.mdpd_get_accel.argtypes = [P, P]
+    L.mdpd_set_state_accel.argtypes = [P, P, P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -357,6 +360,20 @@ def mdpd_describe(h):
     lps = C.c_int32()
     _check(lib().mdpd_describe(h, _p(nc), C.byref(lps)), h)
     return nc.tolist(), int(lps.value)
+
+
+def mdpd_get_accel(h) -> np.ndarray:
+    a = np.zeros((mdpd_num_particles(h), 3))
+    _check(lib().mdpd_get_accel(h, _p(a)), h)
+    return a
+
+
+def mdpd_set_state_accel(h, pos, vel, accel):
+    n = mdpd_num_particles(h)
+    pos = _arr(pos, np.float64, (n, 3))
+    vel = _arr(vel, np.float64, (n, 3))
+    acc = _arr(accel, np.float64, (n, 3))
+    _check(lib().mdpd_set_state_accel(h, _p(pos), _p(vel), _p(acc)), h)
 
 
 def mdpd_density_vjp_dev(h, rhobar_t, xbar_t):

@@ -408,3 +408,33 @@ def test_multi_step_graph_matches_direct_launches(M, precision):
     assert np.array_equal(a.observables(), b.observables())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_checkpoint_resume_is_bitwise(M, precision):
+    """A run checkpointed after 20 steps (positions, velocities, the stored
+    accelerations, the step count, the seed) and resumed in a new handle
+    continues bit for bit; plain set_state (forces re-evaluated with v(t))
+    does not, which is why the accelerations are part of the checkpoint."""
+    w = I.tiny(2000, (7.0, 6.0, 6.5), 33, ntypes=2, g=(0.02, 0.0, 0.0))
+    a, p = make(M, w, precision)
+    a.step(20)
+    x, v, _, _ = a.state()
+    acc = M.mdpd_get_accel(a.h)
+    steps = M.mdpd_step_count(a.h)
+    assert steps == 20
+    b = M.System(p, w.pos, w.vel, w.type, w.seed)
+    M.mdpd_set_step(b.h, steps)
+    M.mdpd_set_state_accel(b.h, x, v, acc)
+    a.step(15)
+    b.step(15)
+    xa, va, _, _ = a.state()
+    xb, vb, _, _ = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb)
+    c = M.System(p, w.pos, w.vel, w.type, w.seed)
+    M.mdpd_set_step(c.h, steps)
+    c.set_state(x, v)
+    c.step(15)
+    assert not np.array_equal(c.state()[1], va)
+    for s in (a, b, c):
+        s.close()
