@@ -413,8 +413,8 @@ void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
                                  h->pos4, h->vel4, h->cell_s);
     else
         launch_rank_gather(st, h->precision, n, h->cap, h->cellof, h->start, h->key, h->src,
-                           master(h, h->cur), master(h, 1 - h->cur), gather_a, h->geo, h->pos4,
-                           h->vel4, h->cell_s);
+                           master(h, h->cur), master(h, 1 - h->cur), gather_a, h->geo, h->ph,
+                           h->pos4, h->vel4, h->cell_s);
     h->cur = 1 - h->cur;
 }
 

@@ -30,7 +30,7 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
     const Rep* rp = nullptr;
     if constexpr (BATCH) {
         const int4 ch = bt.chunks[blockIdx.x];
-        rp = &block_rep<KICK ? REP_SCALARS : REP_GEO>(bt.reps, ch.x);
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);     // the FP32 cell constants too
         i = ch.y + (int)threadIdx.x;
         valid = (int)threadIdx.x < ch.z;
         cell0 = rp->cell0;
@@ -40,19 +40,32 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
     }
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
-    if constexpr (KICK) kick_drift_one(i, cap, geo, BATCH ? rp->ph : ph_p, mk, m, status);
+    const Phys& ph = BATCH ? rp->ph : ph_p;
+    if constexpr (KICK) kick_drift_one(i, cap, geo, ph, mk, m, status);
     int q[3];
     uint32_t st = 0;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const double xk = m.x[k * cap + i];
-        if (!isfinite(xk)) {
+        // FP64 instructions run at 1/64 of the FP32 rate: the cell index is
+        // taken in FP32 and recomputed in FP64 within 2e-3 cell edges of a
+        // face, where FP32 rounding could pick the neighbour (on the axes
+        // fill_derived marks, the FP32 error is below 4e-4 edges), so the
+        // result is always the FP64 one
+        const float t = ((float)xk - ph.df.lo[k]) * ph.df.inv_h[k];
+        if (!isfinite(t)) {
             st |= ST_NONFINITE;
             q[k] = 0;
             continue;
         }
+        int c;
+        const float fl = floorf(t);
+        if (((ph.fast_cell >> k) & 1u) && t - fl > 2e-3f && fl + 1.0f - t > 2e-3f) {
+            c = (int)fl;
+        } else {
+            c = (int)floor((xk - geo.lo[k]) * geo.inv_h[k]);
+        }
         if (!geo.periodic[k] && (xk < geo.lo[k] || xk >= geo.hi[k])) st |= ST_OUT_OF_BOX;
-        int c = (int)floor((xk - geo.lo[k]) * geo.inv_h[k]);
         c = c < 0 ? 0 : (c >= geo.nc[k] ? geo.nc[k] - 1 : c);
         q[k] = c;
     }
@@ -204,7 +217,7 @@ template <typename T, bool BATCH>
 __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ cellof,
                               const uint32_t* __restrict__ start, const uint32_t* __restrict__ key,
                               const uint32_t* __restrict__ src, Master in, Master out,
-                              int gather_a, Geo geo_p, Batch bt,
+                              int gather_a, Geo geo_p, Phys ph_p, Batch bt,
                               typename Vec4<T>::type* __restrict__ pos4,
                               typename Vec4<T>::type* __restrict__ vel4,
                               uint32_t* __restrict__ cell_s)
@@ -217,7 +230,7 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     const Rep* rp = nullptr;
     if constexpr (BATCH) {
         const int4 ch = bt.chunks[blockIdx.x];
-        rp = &block_rep<REP_GEO>(bt.reps, ch.x);
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
         a = ch.y + (int)threadIdx.x;
         valid = (int)threadIdx.x < ch.z;
         cell0 = rp->cell0;
@@ -228,6 +241,7 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     }
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
+    const Phys& ph_g = BATCH ? rp->ph : ph_p;
     const uint32_t i = src[a];
     const uint32_t cg = cellof[i];
     const uint32_t b = start[cg], e = start[cg + 1];
@@ -253,10 +267,12 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     out.id[s] = pid;
     out.type[s] = pt;
     cell_s[s] = c;
+    // offset from the cell centre lo + (q + 1/2) h, taken in FP64 (the
+    // centre as one fused multiply-add on the host-made lo + h/2)
     T off[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        off[k] = (T)(xv[k] - geo.lo[k] - ((double)q[k] + 0.5) * geo.h[k]);
+        off[k] = (T)(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
     pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
     // the random stream is keyed on ids within the replica
     vel4[s] = make4((T)vv[0], (T)vv[1], (T)vv[2], pack_u32(T(0), pid - id0));
@@ -386,16 +402,16 @@ void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uin
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s)
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s)
 {
     if (n <= 0) return;
     if (precision == 0)
         launch_pdl(k_rank_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
-                   start, key, src, in, out, (int)gather_a, geo, Batch{}, (D4*)pos4, (D4*)vel4,
+                   start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (D4*)pos4, (D4*)vel4,
                    cell_s);
     else
         launch_pdl(k_rank_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
-                   start, key, src, in, out, (int)gather_a, geo, Batch{}, (float4*)pos4,
+                   start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (float4*)pos4,
                    (float4*)vel4, cell_s);
 }
 
@@ -408,10 +424,10 @@ void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const
     const dim3 g(bt.nchunk), b(BATCH_CHUNK);
     if (precision == 0)
         launch_pdl_smem(k_rank_gather<double, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
-                        src, in, out, (int)gather_a, Geo{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
+                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
     else
         launch_pdl_smem(k_rank_gather<float, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
-                        src, in, out, (int)gather_a, Geo{}, bt, (float4*)pos4, (float4*)vel4,
+                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (float4*)pos4, (float4*)vel4,
                         cell_s);
 }
 

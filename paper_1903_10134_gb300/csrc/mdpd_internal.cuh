@@ -41,6 +41,9 @@ struct Derived {
     T h[3];          // cell edges
     T hdt;           // dt / 2
     T g[3];          // body force
+    T lo[3];         // box origin
+    T inv_h[3];      // 1 / cell edge
+    T c0[3];         // centre of cell 0: lo + h / 2
 };
 
 // Physical constants of Sec. 2.1 / Eq. 1, tables flattened [ti * 8 + tj].
@@ -53,6 +56,7 @@ struct Phys {
     int rho_self;
     int list_all;                 // 1: the density pass lists partners of frozen particles too
     int prec32;                   // 1: FP32 pair arithmetic (kick increments formed in FP32)
+    uint32_t fast_cell;           // bit k: axis k may take cell indices in FP32 (see k_bin_count)
     void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
     Derived<float> df;
@@ -81,7 +85,17 @@ inline void fill_derived(Phys& ph, const Geo& geo)
     d.inv_sqrt_dt = ph.dt > 0.0 ? 1.0 / std::sqrt(ph.dt) : 0.0;
     for (int k = 0; k < 3; ++k) d.h[k] = geo.h[k];
     d.hdt = 0.5 * ph.dt;
-    for (int k = 0; k < 3; ++k) d.g[k] = ph.g[k];
+    ph.fast_cell = 0;
+    for (int k = 0; k < 3; ++k) {
+        d.g[k] = ph.g[k];
+        d.lo[k] = geo.lo[k];
+        d.inv_h[k] = geo.inv_h[k];
+        d.c0[k] = geo.lo[k] + 0.5 * geo.h[k];
+        // FP32 cell index: few cells and coordinates of moderate size in cell
+        // units, so that the FP32 error stays below 4e-4 cell edges
+        const double span = (std::fabs(geo.lo[k]) + geo.L[k]) * geo.inv_h[k];
+        if (geo.nc[k] <= 1024 && span <= 2048.0) ph.fast_cell |= 1u << k;
+    }
     Derived<float>& f = ph.df;
     f.rc2 = (float)d.rc2;
     f.rd2 = (float)d.rd2;
@@ -92,7 +106,12 @@ inline void fill_derived(Phys& ph, const Geo& geo)
     f.inv_sqrt_dt = (float)d.inv_sqrt_dt;
     for (int k = 0; k < 3; ++k) f.h[k] = (float)d.h[k];
     f.hdt = (float)d.hdt;
-    for (int k = 0; k < 3; ++k) f.g[k] = (float)d.g[k];
+    for (int k = 0; k < 3; ++k) {
+        f.g[k] = (float)d.g[k];
+        f.lo[k] = (float)d.lo[k];
+        f.inv_h[k] = (float)d.inv_h[k];
+        f.c0[k] = (float)d.c0[k];
+    }
 }
 
 // One member of a batch of independent systems: its box and cell lattice,
@@ -229,7 +248,7 @@ void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* o
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, void* pos4, void* vel4, uint32_t* cell_s);
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s);
 void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
                               const uint32_t* start, const uint32_t* key, const uint32_t* src,
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
