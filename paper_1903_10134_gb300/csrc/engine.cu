@@ -37,6 +37,11 @@ struct mdpd_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // a step's observable reduction runs, deferred, on a side stream beside
+    // the next step's binning and density pass
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    bool pending = false;            // the last step's reduction is still to run
     uint64_t seed = 0;
     int precision = 1;
     int64_t n = 0, n_user = 0, cap = 0;
@@ -80,8 +85,9 @@ struct mdpd_handle {
     int64_t steps_host = 0;
 
     // graphs[profiled][mode: 0 fused, 1 last][cur][first half-kick in the binning]
+    //       [previous step's reduction pending]
     bool use_graph = true;
-    Graphs g[2][2][2][2];
+    Graphs g[2][2][2][2][2];
     Graphs gm[2];                    // MULTI_STEPS fused steps in one graph, by cur
     cudaEvent_t tev[EV_PER_STEP] = {};
 
@@ -262,11 +268,12 @@ void destroy_graphs(mdpd_handle* h)
     for (auto& a : h->g)
         for (auto& b : a)
             for (auto& c : b)
-                for (auto& gg : c) {
-                    if (gg.exec) cudaGraphExecDestroy(gg.exec);
-                    if (gg.graph) cudaGraphDestroy(gg.graph);
-                    gg = Graphs();
-                }
+                for (auto& d : c)
+                    for (auto& gg : d) {
+                        if (gg.exec) cudaGraphExecDestroy(gg.exec);
+                        if (gg.graph) cudaGraphDestroy(gg.graph);
+                        gg = Graphs();
+                    }
 }
 
 bool is_fin(double x) { return std::isfinite(x); }
@@ -367,8 +374,11 @@ int status_to_code(uint32_t st)
 
 // Synchronise the stream and turn the device status word into an error code
 // (the word is cleared).
+void flush_pending(mdpd_handle* h);
+
 int sync_check(mdpd_handle* h)
 {
+    flush_pending(h);
     CK(cudaStreamSynchronize(h->stream));
     uint32_t st = 0;
     CK(cudaMemcpy(&st, h->status, sizeof(st), cudaMemcpyDeviceToHost));
@@ -469,33 +479,54 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out,
                      master(h, h->cur), out, h->partials, h->status);
 }
 
-void enqueue_reduce(mdpd_handle* h, int advance)
+void enqueue_reduce(mdpd_handle* h, int advance, cudaStream_t st = nullptr)
 {
+    if (!st) st = h->stream;
     if (h->nrep) {
-        launch_reduce_obs_batch(h->stream, h->precision, h->partials, h->nchunk * PAIR_BLOCK_WARPS,
+        launch_reduce_obs_batch(st, h->precision, h->partials, h->nchunk * PAIR_BLOCK_WARPS,
                                 h->d_wr, h->nrep, h->red_ticket, h->obs_b, h->step, advance);
         return;
     }
     const int lpp = h->kernels == MDPD_KERNELS_SCAN ? 1 : h->force_lpp;
-    launch_reduce_obs(h->stream, h->precision, h->partials, obs_num_partials((int)h->n, lpp),
+    launch_reduce_obs(st, h->precision, h->partials, obs_num_partials((int)h->n, lpp),
                       h->red_l1,
                       h->red_ticket, h->obs, h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS,
                       h->step, advance);
 }
 
+// The last step's observable reduction, if it has not run yet: enqueued
+// before anything reads the observables or the step counter, or overwrites
+// the force pass's partials outside the time-step loop.
+void flush_pending(mdpd_handle* h)
+{
+    if (!h->pending) return;
+    h->pending = false;
+    enqueue_reduce(h, 1);
+}
+
 // One velocity-Verlet step: bin (after the first half-kick and drift when
 // `kick`; otherwise the previous step's force pass did them), density, force
-// (+ half-kick [+ next half-kick, drift]), reduction.
-void enqueue_step(mdpd_handle* h, ForceMode mode, bool kick, cudaEvent_t* evs)
+// (+ half-kick [+ next half-kick, drift]).  The step's own reduction is left
+// pending.  With `pend` the previous step's reduction runs on the side stream
+// beside this binning and density pass and joins before this force pass,
+// which reads the step counter the reduction advances and overwrites the
+// partials it reads.
+void enqueue_step(mdpd_handle* h, ForceMode mode, bool kick, cudaEvent_t* evs, bool pend)
 {
     record(h, evs, 0);
+    if (pend) {
+        cudaEventRecord(h->fork_ev, h->stream);
+        cudaStreamWaitEvent(h->side, h->fork_ev, 0);
+        enqueue_reduce(h, 1, h->side);
+        cudaEventRecord(h->join_ev, h->side);
+    }
     enqueue_bin(h, false, kick);
     record(h, evs, 1);
     enqueue_density(h);
     record(h, evs, 2);
+    if (pend) cudaStreamWaitEvent(h->stream, h->join_ev, 0);
     enqueue_force(h, mode, 1, nullptr);
     record(h, evs, 3);
-    enqueue_reduce(h, 1);
     record(h, evs, 4);
 }
 
@@ -504,6 +535,7 @@ void enqueue_step(mdpd_handle* h, ForceMode mode, bool kick, cudaEvent_t* evs)
 // integration acceleration a.
 int evaluate(mdpd_handle* h, double* out, bool keep_a)
 {
+    flush_pending(h);
     enqueue_bin(h, keep_a);
     enqueue_density(h);
     enqueue_force(h, FM_EVAL, 0, out ? out : h->a[h->cur]);
@@ -523,7 +555,7 @@ int capture_multi(mdpd_handle* h, int cur)
     const int saved = h->cur;
     h->cur = cur;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < MULTI_STEPS; ++k) enqueue_step(h, FM_FUSED, false, nullptr);
+    for (int k = 0; k < MULTI_STEPS; ++k) enqueue_step(h, FM_FUSED, false, nullptr, true);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     h->cur = saved;
@@ -539,13 +571,14 @@ int capture_multi(mdpd_handle* h, int cur)
     return MDPD_OK;
 }
 
-int capture_step(mdpd_handle* h, int prof, int mode, int cur, int kick)
+int capture_step(mdpd_handle* h, int prof, int mode, int cur, int kick, int pend)
 {
-    Graphs& gg = h->g[prof][mode][cur][kick];
+    Graphs& gg = h->g[prof][mode][cur][kick][pend];
     const int saved = h->cur;
     h->cur = cur;
     CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_step(h, mode == 0 ? FM_FUSED : FM_LAST, kick != 0, prof ? h->tev : nullptr);
+    enqueue_step(h, mode == 0 ? FM_FUSED : FM_LAST, kick != 0, prof ? h->tev : nullptr,
+                 pend != 0);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->stream, &graph);
     h->cur = saved;
@@ -589,16 +622,18 @@ int run_step(mdpd_handle* h, ForceMode mode, bool kick)
 {
     cudaEvent_t* evs = next_prof_events(h);
     h->prof_launches += step_launches(h);
+    const bool pend = h->pending;
+    h->pending = true;
     if (!h->use_graph) {
-        enqueue_step(h, mode, kick, evs);
+        enqueue_step(h, mode, kick, evs, pend);
         CK(cudaGetLastError());
         return MDPD_OK;
     }
     const int prof = evs ? 1 : 0;
     const int mi = mode == FM_FUSED ? 0 : 1;
-    Graphs& gg = h->g[prof][mi][h->cur][kick ? 1 : 0];
+    Graphs& gg = h->g[prof][mi][h->cur][kick ? 1 : 0][pend ? 1 : 0];
     if (!gg.exec) {
-        int rc = capture_step(h, prof, mi, h->cur, kick ? 1 : 0);
+        int rc = capture_step(h, prof, mi, h->cur, kick ? 1 : 0, pend ? 1 : 0);
         if (rc) return rc;
     }
     if (prof)
@@ -694,6 +729,12 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
             h->err = "cudaEventCreate failed";
             return bail(MDPD_ERR_CUDA);
         }
+    if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+        h->err = "side stream or event creation failed";
+        return bail(MDPD_ERR_CUDA);
+    }
 
     // upload: positions to fout, velocities to x[1] (both 3n staging), types
     std::vector<uint8_t> t8((size_t)n);
@@ -1075,7 +1116,8 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     // the first step's binning applies the first half-kick and drift; later
     // steps get them from the previous force pass (FM_FUSED)
     for (int64_t k = 0; k < nsteps; ++k) {
-        const bool middle = k > 0 && k + MULTI_STEPS < nsteps;    // fused, no kick
+        // fused, no kick, with the previous step's reduction still pending
+        const bool middle = k > 0 && k + MULTI_STEPS < nsteps && h->pending;
         if (middle && h->use_graph && h->prof_used >= h->prof_cap) {
             Graphs& gg = h->gm[h->cur];
             if (!gg.exec) {
@@ -1302,6 +1344,7 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs)
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
+    flush_pending(h);      // the pending reduction reads the current partials layout
     switch (option) {
     case MDPD_OPT_GRAPH:
         h->use_graph = value != 0;
@@ -1380,6 +1423,7 @@ int mdpd_set_params(mdpd_handle* h, const mdpd_params* p)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "batch handle: use mdpd_batch_set_params");
+    flush_pending(h);
     std::string why;
     int rc = validate_params(p, why);
     if (rc) return h->fail(rc, why);
@@ -1600,6 +1644,9 @@ void mdpd_destroy(mdpd_handle* h)
     for (auto& e : h->tev)
         if (e) cudaEventDestroy(e);
     for (auto e : h->prof_ev) cudaEventDestroy(e);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
+    if (h->side) cudaStreamDestroy(h->side);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
