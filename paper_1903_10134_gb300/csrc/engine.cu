@@ -64,6 +64,11 @@ struct mdpd_handle {
     // binning
     uint32_t *count = nullptr, *start = nullptr, *cellof = nullptr, *slot = nullptr;
     uint32_t *key = nullptr, *src = nullptr, *scan_tmp = nullptr;
+    uint32_t* mend = nullptr;        // first frozen slot of each cell (see launch_rank_gather)
+    // frozen-frozen part of each frozen particle's density, by id (constant
+    // while the frozen particles and r_d stay; recomputed when ff_dirty)
+    void* rho_ff = nullptr;
+    bool ff_dirty = true;
     // misc
     uint32_t* status = nullptr;
     uint64_t* step = nullptr;
@@ -195,6 +200,7 @@ void free_particles(mdpd_handle* h)
     dfree(h->nl);
     dfree(h->nl_count);
     dfree(h->phi);
+    dfree(h->rho_ff);
 }
 
 int alloc_particles(mdpd_handle* h, int64_t cap)
@@ -226,6 +232,7 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->nl, (size_t)NL_SLOTS * c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->nl_count, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->phi, c * tsz);
+    if (!rc) rc = dalloc(h, &h->rho_ff, c * tsz);
     if (!rc) h->cap = (int64_t)c;
     return rc;
 }
@@ -255,6 +262,7 @@ void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
     std::swap(a->nl, b->nl);
     std::swap(a->nl_count, b->nl_count);
     std::swap(a->phi, b->phi);
+    std::swap(a->rho_ff, b->rho_ff);
     std::swap(a->cap, b->cap);
 }
 
@@ -420,11 +428,11 @@ void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
     if (h->nrep)
         launch_rank_gather_batch(st, h->precision, h->cap, h->cellof, h->start, h->key, h->src,
                                  master(h, h->cur), master(h, 1 - h->cur), gather_a, h->batch(),
-                                 h->pos4, h->vel4, h->cell_s);
+                                 h->pos4, h->vel4, h->cell_s, h->mend);
     else
         launch_rank_gather(st, h->precision, n, h->cap, h->cellof, h->start, h->key, h->src,
                            master(h, h->cur), master(h, 1 - h->cur), gather_a, h->geo, h->ph,
-                           h->pos4, h->vel4, h->cell_s);
+                           h->pos4, h->vel4, h->cell_s, h->mend);
     h->cur = 1 - h->cur;
 }
 
@@ -433,6 +441,25 @@ void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
 int step_launches(const mdpd_handle* h)
 {
     return 6 + scan_num_launches(h->geo.ncell);
+}
+
+// The thread-per-particle density pass of a system with frozen particles
+// scans only mobile candidates for frozen homes (frozen split).
+bool use_split(const mdpd_handle* h)
+{
+    return !h->nrep && h->ph.frozen != 0 && !h->ph.list_all &&
+           (h->want_phi || h->kernels == MDPD_KERNELS_NLIST_THREAD);
+}
+
+// The frozen-frozen density part, from the last binning (the frozen
+// particles have not moved since), when the split needs it and it is stale.
+void ensure_ff(mdpd_handle* h)
+{
+    if (!use_split(h) || !h->ff_dirty) return;
+    launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
+                      h->cell_s, h->start, h->rho, h->nl, h->nl_count, 2, h->mend, h->id[h->cur],
+                      h->rho_ff);
+    h->ff_dirty = false;
 }
 
 void enqueue_density(mdpd_handle* h)
@@ -448,15 +475,15 @@ void enqueue_density(mdpd_handle* h)
         return;
     }
     h->ph.phi_out = h->want_phi ? h->phi : nullptr;
-    if (h->want_phi)              // the wall density is accumulated by this variant only
+    const int fs = use_split(h) ? 1 : 0;
+    if (h->want_phi || h->kernels == MDPD_KERNELS_NLIST_THREAD)
+        // (the wall density is accumulated by this variant only)
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
-                          h->cell_s, h->start, h->rho, h->nl, h->nl_count);
+                          h->cell_s, h->start, h->rho, h->nl, h->nl_count, fs, h->mend,
+                          h->id[h->cur], h->rho_ff);
     else if (cell)
         launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph, h->pos4,
                             h->start, h->rho, h->nl, h->nl_count);
-    else if (h->kernels == MDPD_KERNELS_NLIST_THREAD)
-        launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
-                          h->cell_s, h->start, h->rho, h->nl, h->nl_count);
     else
         launch_density(h->stream, h->precision, (int)h->n, h->geo, h->ph, h->pos4, h->cell_s,
                        h->start, h->rho);
@@ -537,6 +564,7 @@ int evaluate(mdpd_handle* h, double* out, bool keep_a)
 {
     flush_pending(h);
     enqueue_bin(h, keep_a);
+    ensure_ff(h);
     enqueue_density(h);
     enqueue_force(h, FM_EVAL, 0, out ? out : h->a[h->cur]);
     enqueue_reduce(h, 0);
@@ -718,6 +746,7 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
     const int64_t nb = scan_num_blocks(h->geo.ncell);
     if ((rc = dalloc(h, &h->count, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->start, (size_t)(h->geo.ncell + 1) * sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->mend, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->scan_tmp, (size_t)(nb + 1) * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->status, sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->step, sizeof(uint64_t))) ||
@@ -1103,6 +1132,7 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
         h->mk.inv_voxel_exact = std::frexp(voxel, &ex) == 0.5 ? 1 : 0;
     }
     h->walls_set = true;
+    h->ff_dirty = true;
     destroy_graphs(h);
     if ((rc = evaluate(h, nullptr, false))) return rc;
     return sync_check(h);
@@ -1113,6 +1143,7 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return MDPD_OK;
+    ensure_ff(h);
     // the first step's binning applies the first half-kick and drift; later
     // steps get them from the previous force pass (FM_FUSED)
     for (int64_t k = 0; k < nsteps; ++k) {
@@ -1237,7 +1268,14 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
     else
         launch_load_state(st, n, h->cap, d_pos, d_vel, d_acc, h->geo, master(h, c), h->type_by_id,
                           h->status);
+    h->ff_dirty = true;                      // the frozen particles may have moved
     if (acc) {
+        // no evaluation; a binning (the accelerations gathered along) gives
+        // the frozen-frozen density part its cell order
+        if (use_split(h)) {
+            enqueue_bin(h, true);
+            ensure_ff(h);
+        }
         CK(cudaGetLastError());
         return MDPD_OK;
     }
@@ -1437,6 +1475,7 @@ int mdpd_set_params(mdpd_handle* h, const mdpd_params* p)
     if ((rc = sync_check(h))) return rc;
     h->p = *p;
     setup_geo_phys(h);
+    h->ff_dirty = true;                      // r_d or the frozen types may change
     destroy_graphs(h);
     return MDPD_OK;
 }
@@ -1574,6 +1613,7 @@ int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
     enqueue_bin(h, true);                     // same positions: same order, state kept
     for (int v = 0; v < 2; ++v) {
         h->kernels = variants[v];
+        ensure_ff(h);
         const double t = time_it([&] { enqueue_density(h); });
         if (t < 0) return done(MDPD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
         if (ms) ms[v] = t;
@@ -1630,6 +1670,7 @@ void mdpd_destroy(mdpd_handle* h)
     free_particles(h);
     dfree(h->count);
     dfree(h->start);
+    dfree(h->mend);
     dfree(h->scan_tmp);
     dfree(h->status);
     dfree(h->step);

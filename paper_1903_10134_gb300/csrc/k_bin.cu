@@ -1,9 +1,10 @@
 // Cell binning by a counting sort (per step): cell id of every particle (with
 // the step's first half-kick and drift when asked), per-cell counts, an
 // exclusive scan, a scatter in atomic order, and one kernel that ranks each
-// particle inside its cell by id (so the order inside a cell does not depend
-// on the order of the atomics) and gathers the state into that order with
-// positions re-expressed as offsets from the cell centre.
+// particle inside its cell by (frozen, id) (so the order inside a cell does
+// not depend on the order of the atomics, and a cell's mobile particles come
+// first) and gathers the state into that order with positions re-expressed as
+// offsets from the cell centre.
 #include "pair.cuh"
 
 namespace mdpd {
@@ -72,7 +73,10 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
     if (st) atomicOr(status, st);
     const uint32_t c = (uint32_t)(cell0 + q[0] + geo.nc[0] * (q[1] + geo.nc[1] * q[2]));
     cellof[i] = c;
-    slot[i] = atomicAdd(&count[c], 1u);
+    // arrival slot, with the frozen flag in the top bit (it orders a cell's
+    // frozen particles after its mobile ones)
+    const uint32_t fz = (ph.frozen >> m.type[i]) & 1u;
+    slot[i] = atomicAdd(&count[c], 1u) | (fz << 31);
 }
 
 // ---- exclusive scan ------------------------------------------------------------
@@ -177,8 +181,9 @@ __global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint32_t dst = start[cellof[i]] + slot[i];
-    key[dst] = id[i];
+    const uint32_t sl = slot[i];
+    const uint32_t dst = start[cellof[i]] + (sl & 0x7fffffffu);
+    key[dst] = id[i] | (sl & 0x80000000u);
     src[dst] = (uint32_t)i;
 }
 
@@ -206,8 +211,10 @@ __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
     }
 }
 
-// Order inside each cell by particle id, fused with the gather into cell
-// order.  The scatter filled slot a (in atomic order) with key[a] = id and
+// Order inside each cell by (frozen, particle id), fused with the gather into
+// cell order; the first particle of each cell also records where the cell's
+// frozen particles begin (mend).  The scatter filled slot a (in atomic order)
+// with key[a] = frozen << 31 | id and
 // src[a] = the particle's master index i; the particle's place in its cell c
 // is s = start[c] + (number of keys of the cell below key[a]), and the thread
 // copies particle i's master state to slot s of the other buffer and writes
@@ -220,7 +227,7 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
                               int gather_a, Geo geo_p, Phys ph_p, Batch bt,
                               typename Vec4<T>::type* __restrict__ pos4,
                               typename Vec4<T>::type* __restrict__ vel4,
-                              uint32_t* __restrict__ cell_s)
+                              uint32_t* __restrict__ cell_s, uint32_t* __restrict__ mend)
 {
     pdl_enter();
     int a;
@@ -246,9 +253,15 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     const uint32_t cg = cellof[i];
     const uint32_t b = start[cg], e = start[cg + 1];
     const uint32_t kk = key[a];
-    uint32_t r = 0;
-    for (uint32_t q = b; q < e; ++q) r += key[q] < kk ? 1u : 0u;
+    uint32_t r = 0, nm = 0;
+    for (uint32_t q = b; q < e; ++q) {
+        const uint32_t kq = key[q];
+        r += kq < kk ? 1u : 0u;
+        nm += kq < 0x80000000u ? 1u : 0u;
+    }
     const uint32_t s = b + r;
+    // cells without particles keep a stale mend: readers clamp it to [b, e]
+    if (r == 0) mend[cg] = b + nm;
     const uint32_t c = cg - (uint32_t)cell0;      // cell within the replica
     const int q[3] = { (int)(c % (uint32_t)geo.nc[0]),
                        (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]),
@@ -402,33 +415,34 @@ void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uin
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s)
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s,
+                        uint32_t* mend)
 {
     if (n <= 0) return;
     if (precision == 0)
         launch_pdl(k_rank_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
                    start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (D4*)pos4, (D4*)vel4,
-                   cell_s);
+                   cell_s, mend);
     else
         launch_pdl(k_rank_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
                    start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (float4*)pos4,
-                   (float4*)vel4, cell_s);
+                   (float4*)vel4, cell_s, mend);
 }
 
 void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
                               const uint32_t* start, const uint32_t* key, const uint32_t* src,
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
-                              void* pos4, void* vel4, uint32_t* cell_s)
+                              void* pos4, void* vel4, uint32_t* cell_s, uint32_t* mend)
 {
     if (bt.nchunk <= 0) return;
     const dim3 g(bt.nchunk), b(BATCH_CHUNK);
     if (precision == 0)
         launch_pdl_smem(k_rank_gather<double, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
-                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
+                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (D4*)pos4, (D4*)vel4, cell_s, mend);
     else
         launch_pdl_smem(k_rank_gather<float, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
                         src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (float4*)pos4, (float4*)vel4,
-                        cell_s);
+                        cell_s, mend);
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,

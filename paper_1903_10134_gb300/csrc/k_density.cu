@@ -29,13 +29,25 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 // evaluated under a branch: on the large porous systems this variant is picked
 // for, most warps have no candidate within r_d in an iteration, and a
 // branch-free weight (a reciprocal square root per candidate) measured slower.
-template <typename T, bool BATCH, bool WANT_PHI>
+//
+// Frozen split (FS, single systems with frozen particles).  Frozen particles
+// never move, so the part of a frozen particle's density that comes from
+// frozen neighbours is a constant: FS = 2 computes it once (frozen homes,
+// frozen candidates only) into rho_ff[id]; FS = 1 then scans only the mobile
+// slots [b, mend) of each neighbour cell for frozen homes and adds rho_ff.  With FS = 1 each block first moves its mobile homes
+// onto the leading lanes, so that warps of frozen homes run the short scans
+// together.  Homes with partner lists (mobile, or every home under list_all)
+// scan everything.
+template <typename T, bool BATCH, bool WANT_PHI, int FS>
 __global__ void __launch_bounds__(PAIR_BLOCK, 12)
 k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
              const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
              const uint32_t* __restrict__ start, T* __restrict__ rho_out,
-             uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count)
+             uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count,
+             const uint32_t* __restrict__ mend, const uint32_t* __restrict__ id_s,
+             T* __restrict__ rho_ff)
 {
+    static_assert(FS == 0 || !BATCH, "the frozen split is for single systems");
     pdl_enter();
     int s;
     bool valid;
@@ -51,6 +63,35 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
         s = blockIdx.x * blockDim.x + threadIdx.x;
         valid = s < n;
     }
+    if constexpr (FS == 1) {
+        // mobile homes first, then frozen ones, each in slot order
+        __shared__ int act[PAIR_BLOCK];
+        __shared__ uint32_t wcnt[2][PAIR_BLOCK / 32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const bool mob = valid && (ph_p.list_all ||
+                                   ((ph_p.frozen >> unpack_u32(pos4[s].w)) & 1u) == 0u);
+        const unsigned bm = __ballot_sync(0xffffffffu, mob);
+        const unsigned bf = __ballot_sync(0xffffffffu, valid && !mob);
+        if (lane == 0) {
+            wcnt[0][warp] = (uint32_t)__popc(bm);
+            wcnt[1][warp] = (uint32_t)__popc(bf);
+        }
+        __syncthreads();
+        uint32_t om = 0, of = 0, nmob = 0, nall = 0;
+#pragma unroll
+        for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
+            om += w < warp ? wcnt[0][w] : 0u;
+            of += w < warp ? wcnt[1][w] : 0u;
+            nmob += wcnt[0][w];
+            nall += wcnt[0][w] + wcnt[1][w];
+        }
+        const unsigned lt = (1u << lane) - 1u;
+        if (mob) act[om + __popc(bm & lt)] = s;
+        else if (valid) act[nmob + of + __popc(bf & lt)] = s;
+        __syncthreads();
+        valid = threadIdx.x < nall;
+        if (valid) s = act[threadIdx.x];
+    }
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
     const Phys& ph = BATCH ? rp->ph : ph_p;
@@ -61,6 +102,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     const auto pi = pos4[s];
     const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     const bool mobile = ph.list_all || mob_true;
+    if (FS == 2 && mobile) return;              // the frozen-frozen part only
     // wall density of a mobile particle (WANT_PHI): sum over frozen partners
     // within r_c of 15/(2 pi r_c^3) (1 - r/r_c)^2
     const bool want_phi = WANT_PHI && mob_true;
@@ -69,7 +111,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     T phi = T(0);
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
-    T acc = ph.rho_self ? cw : T(0);
+    T acc = (FS != 2 && ph.rho_self) ? cw : T(0);
     uint32_t cnt = 0;
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
@@ -85,7 +127,8 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 const T sx = pi.x - (T)ox * dc.h[0];
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
                 const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
-                const uint32_t b = start[nc], e = start[nc + 1];
+                uint32_t b = start[nc], e = start[nc + 1];
+                if (FS == 1 && !mobile) e = min(max(mend[nc], b), e);     // mobile slots
                 // the common path is one distance test: r_d <= r_c, so the
                 // density term, the list append and the self check all sit
                 // inside the r < r_c branch (about 15 % of the candidates)
@@ -94,7 +137,10 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                     const auto pj = pos4[j];
                     const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
                     const T r2 = dx * dx + dy * dy + dz * dz;
-                    if (r2 < rc2 && j != (uint32_t)s) {
+                    // (FS = 2 takes frozen candidates only, by type, so it does not
+                    // depend on the frozen types the binning ordered by)
+                    if (r2 < rc2 && j != (uint32_t)s &&
+                        (FS != 2 || ((ph.frozen >> unpack_u32(pj.w)) & 1u))) {
                         if (r2 < rd2) {        // r = 0 (a coincident particle) gives w(0)
                             const T w = T(1) - sqrt0_t(r2) * inv_rd;
                             acc += cw * w * w;
@@ -112,6 +158,11 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
             }
         }
     }
+    if constexpr (FS == 2) {
+        rho_ff[id_s[s]] = acc;
+        return;
+    }
+    if (FS == 1 && !mobile) acc += rho_ff[id_s[s]];
     rho_out[s] = acc;
     nl_count[s] = cnt;
     if (WANT_PHI) ((T*)ph.phi_out)[s] = phi;
@@ -301,21 +352,34 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
 
 }  // namespace
 
-void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
-                       const Phys& ph, const void* pos4, const uint32_t* cell_s,
-                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count)
+template <typename T>
+void density_nl_t(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
+                  const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho,
+                  uint32_t* nl, uint32_t* nl_count, int fs, const uint32_t* mend,
+                  const uint32_t* id_s, void* rho_ff)
 {
-    if (n <= 0) return;
+    using V = typename Vec4<T>::type;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
     const bool phi = ph.phi_out != nullptr;
+    auto k = phi ? k_density_nl<T, false, true, 0> : k_density_nl<T, false, false, 0>;
+    if (fs == 1) k = phi ? k_density_nl<T, false, true, 1> : k_density_nl<T, false, false, 1>;
+    if (fs == 2) k = k_density_nl<T, false, false, 2>;
+    launch_pdl(k, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const V*)pos4, cell_s,
+               start, (T*)rho, nl, nl_count, mend, id_s, (T*)rho_ff);
+}
+
+void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                       const Phys& ph, const void* pos4, const uint32_t* cell_s,
+                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
+                       int fs, const uint32_t* mend, const uint32_t* id_s, void* rho_ff)
+{
+    if (n <= 0) return;
     if (precision == 0)
-        launch_pdl(phi ? k_density_nl<double, false, true> : k_density_nl<double, false, false>,
-                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const D4*)pos4,
-                   cell_s, start, (double*)rho, nl, nl_count);
+        density_nl_t<double>(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend,
+                             id_s, rho_ff);
     else
-        launch_pdl(phi ? k_density_nl<float, false, true> : k_density_nl<float, false, false>,
-                   dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const float4*)pos4,
-                   cell_s, start, (float*)rho, nl, nl_count);
+        density_nl_t<float>(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend,
+                            id_s, rho_ff);
 }
 
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
@@ -325,11 +389,13 @@ void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const 
     if (bt.nchunk <= 0) return;
     const dim3 g(bt.nchunk), b(PAIR_BLOCK);
     if (precision == 0)
-        launch_pdl_smem(k_density_nl<double, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
-                        bt, (const D4*)pos4, cell_s, start, (double*)rho, nl, nl_count);
+        launch_pdl_smem(k_density_nl<double, true, false, 0>, g, b, REP_SMEM, st, 0, cap, Geo{},
+                        Phys{}, bt, (const D4*)pos4, cell_s, start, (double*)rho, nl, nl_count,
+                        nullptr, nullptr, nullptr);
     else
-        launch_pdl_smem(k_density_nl<float, true, false>, g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{},
-                        bt, (const float4*)pos4, cell_s, start, (float*)rho, nl, nl_count);
+        launch_pdl_smem(k_density_nl<float, true, false, 0>, g, b, REP_SMEM, st, 0, cap, Geo{},
+                        Phys{}, bt, (const float4*)pos4, cell_s, start, (float*)rho, nl, nl_count,
+                        nullptr, nullptr, nullptr);
 }
 
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,

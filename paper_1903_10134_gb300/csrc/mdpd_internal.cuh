@@ -243,16 +243,19 @@ int scan_num_launches(int64_t n);
 void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
                            bool zero_in = false);
 // For every scattered slot a: the particle's place s in its cell (rank of
-// key[a] = id among the cell's keys), and the gather of master state in[src[a]]
-// to out[s] with the cell-ordered compute arrays (pos4, vel4, cell_s).
+// key[a] = frozen << 31 | id among the cell's keys), and the gather of master
+// state in[src[a]] to out[s] with the cell-ordered compute arrays (pos4, vel4,
+// cell_s).  mend[c]: first frozen slot of every non-empty cell c (stale for
+// empty cells: clamp to [start[c], start[c + 1]]).
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s);
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s,
+                        uint32_t* mend);
 void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
                               const uint32_t* start, const uint32_t* key, const uint32_t* src,
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
-                              void* pos4, void* vel4, uint32_t* cell_s);
+                              void* pos4, void* vel4, uint32_t* cell_s, uint32_t* mend);
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
                         const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src);
 // Sorts each cell's slots by key and clears count[] for the next binning.
@@ -273,9 +276,15 @@ int force_num_blocks(int n, int lpp = 1);
 int obs_num_partials(int n, int lpp = 1);
 // Density pass that also writes the force partners of mobile particles
 // (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
+// fs (frozen split; mend from the binning, id_s the cell-ordered ids, rho_ff
+// cap values of the pass's type indexed by id): 0 full scans; 2 writes the
+// frozen-frozen part of every frozen particle's density to rho_ff; 1 scans
+// only mobile candidates for frozen homes and adds rho_ff.
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
-                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count);
+                       const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
+                       int fs = 0, const uint32_t* mend = nullptr, const uint32_t* id_s = nullptr,
+                       void* rho_ff = nullptr);
 // Warp-per-cell variant of launch_density_nl (same outputs).
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
                          const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,

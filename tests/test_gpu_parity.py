@@ -438,3 +438,57 @@ def test_checkpoint_resume_is_bitwise(M, precision):
     assert not np.array_equal(c.state()[1], va)
     for s in (a, b, c):
         s.close()
+
+
+def _rock_thread(M, precision, seed=5):
+    w = I.rock(nvox=32, voxel=0.5, corr=4.0, porosity=0.3, g=0.5, seed=seed, precision=precision)
+    s = M.System.from_workload(w, precision=precision)
+    s.set_option(M.OPT_KERNELS, M.KERNELS_NLIST_THREAD)
+    return w, s
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_frozen_split_density_tracks_oracle(M, precision):
+    """With frozen wall particles the thread-per-particle density pass scans
+    only the mobile candidates of a frozen home and adds the home's
+    frozen-frozen part, computed once: the densities of all particles (fluid
+    and wall) stay equal to the oracle's as the fluid moves."""
+    w, s = _rock_thread(M, precision)
+    nwall = 0
+    for k in range(3):
+        s.step(6)
+        x, v, t, rho = s.state()
+        nwall = int(np.sum(t == w.wall_type))
+        o = O.Oracle(w.params.copy(precision=0), x, v, t, w.seed, use_cells=True)
+        err = np.abs(rho - o.rho)
+        assert err.max() <= RHO_TOL[precision] * max(1.0, o.rho.max()), err.max()
+    assert nwall > 1000                      # the split had frozen homes to work on
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_frozen_split_graph_direct_and_resume_bitwise(M, precision):
+    """On a walled system with the split density pass: graph replay equals
+    direct launches bit for bit, and a checkpoint resumed in a new handle
+    (whose frozen-frozen densities are recomputed there) continues bit for
+    bit."""
+    w, a = _rock_thread(M, precision)
+    _, b = _rock_thread(M, precision)
+    b.set_option(M.OPT_GRAPH, 0)
+    for s in (a, b):
+        s.step(19)
+    xa, va, _, ra = a.state()
+    xb, vb, _, rb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+    acc = M.mdpd_get_accel(a.h)
+    steps = M.mdpd_step_count(a.h)
+    _, c = _rock_thread(M, precision)
+    M.mdpd_set_step(c.h, steps)
+    M.mdpd_set_state_accel(c.h, xa, va, acc)
+    a.step(11)
+    c.step(11)
+    xa, va, _, ra = a.state()
+    xc, vc, _, rc = c.state()
+    assert np.array_equal(xa, xc) and np.array_equal(va, vc) and np.array_equal(ra, rc)
+    for s in (a, b, c):
+        s.close()
