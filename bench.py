@@ -210,18 +210,20 @@ def kernel_traffic(workload: str, precision: str) -> dict:
     return out
 
 
-def candidate_tests(x, params, ncell) -> int:
-    """Candidate tests of one density pass: every particle is tested against
-    every particle of its 27 neighbour cells (itself included), so the count
-    is sum over cells c of n_c times the particles in c's neighbourhood."""
+def _cell_counts(x, params, nc):
     import numpy as np
-    nc = np.array(ncell, dtype=np.int64)
     lo = np.array(params.box_lo, dtype=float)
     L = np.array(params.box, dtype=float)
     q = np.floor((x - lo) / (L / nc)).astype(np.int64)
     q = np.clip(q, 0, nc - 1)
     counts = np.zeros(tuple(nc[::-1]), dtype=np.int64)       # [z, y, x]
     np.add.at(counts, (q[:, 2], q[:, 1], q[:, 0]), 1)
+    return counts
+
+
+def _neighbourhood_sum(counts, periodic):
+    """For every cell, the sum of counts over its 27 neighbour cells."""
+    import numpy as np
     neigh = np.zeros_like(counts)
     for oz in (-1, 0, 1):
         for oy in (-1, 0, 1):
@@ -230,7 +232,7 @@ def candidate_tests(x, params, ncell) -> int:
                 for axis, o, k in ((0, oz, 2), (1, oy, 1), (2, ox, 0)):
                     if o == 0:
                         continue
-                    if params.periodic[k]:
+                    if periodic[k]:
                         sh = np.roll(sh, -o, axis=axis)
                     else:
                         pad = np.zeros_like(sh)
@@ -245,7 +247,24 @@ def candidate_tests(x, params, ncell) -> int:
                         pad[tuple(idx)] = sh[tuple(src)]
                         sh = pad
                 neigh += sh
-    return int((counts * neigh).sum())
+    return neigh
+
+
+def candidate_tests(x, params, ncell, frozen=None) -> int:
+    """Candidate tests of one density pass: every particle is tested against
+    every particle of its 27 neighbour cells (itself included), so the count
+    is sum over cells c of n_c times the particles in c's neighbourhood.  With
+    `frozen` (a per-particle flag; the split density pass), a frozen particle
+    is tested against the mobile particles of its neighbourhood only."""
+    import numpy as np
+    nc = np.array(ncell, dtype=np.int64)
+    counts = _cell_counts(x, params, nc)
+    neigh = _neighbourhood_sum(counts, params.periodic)
+    if frozen is None or not np.any(frozen):
+        return int((counts * neigh).sum())
+    cf = _cell_counts(x[frozen], params, nc)
+    cm = counts - cf
+    return int((cm * neigh).sum() + (cf * _neighbourhood_sum(cm, params.periodic)).sum())
 
 
 OBS_NAMES = ("px", "py", "pz", "ke", "kT", "Wxx", "Wyy", "Wzz", "Wxy", "Wxz", "Wyz",
@@ -522,15 +541,22 @@ def run_ours(args):
     cand = None
     if rank == 0:
         import numpy as np
-        xs = s.state()[0]
+        xs, _, ts, _ = s.state()
         ws = w if args.workload == "batch" else [w]
+        split_density = (tuned and tuned["chosen"] == "nlist-thread") or \
+            args.kernels == "nlist-thread"
         off = 0
         cand = 0
         for wr in ws:
             nr = wr.n if args.workload == "batch" else n
             p = wr.params
             ncell = [max(1, int(math.floor(p.box[k] / p.rc))) for k in range(3)]
-            cand += candidate_tests(xs[off:off + nr], p, ncell)
+            # the thread-per-particle pass of a single system with frozen
+            # particles runs the frozen split
+            fz = None
+            if args.workload != "batch" and p.frozen_types and split_density:
+                fz = np.isin(ts[off:off + nr], np.array(p.frozen_types))
+            cand += candidate_tests(xs[off:off + nr], p, ncell, fz)
             off += nr
 
     # end-to-end through the host-pointer C ABI: per step upload x, v from

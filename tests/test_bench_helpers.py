@@ -42,3 +42,33 @@ def test_candidate_count_matches_direct_count(periodic):
                     ok = False
             want += ok
     assert got == want
+
+
+def test_split_candidate_count_matches_direct_count():
+    """With frozen particles (the split density pass) a frozen home is tested
+    against mobile candidates only."""
+    B = _bench()
+    rng = np.random.default_rng(5)
+    p = I.MDPDParams(box=(5.0, 4.2, 6.1), periodic=(1, 1, 0))
+    n = 300
+    x = rng.random((n, 3)) * np.array(p.box)
+    frozen = rng.random(n) < 0.4
+    nc = [max(1, int(math.floor(p.box[k] / p.rc))) for k in range(3)]
+    got = B.candidate_tests(x, p, nc, frozen)
+    h = np.array(p.box) / nc
+    q = np.clip(np.floor(x / h).astype(int), 0, np.array(nc) - 1)
+    want = 0
+    for i in range(n):
+        for j in range(n):
+            if frozen[i] and frozen[j]:
+                continue
+            ok = True
+            for k in range(3):
+                d = q[j, k] - q[i, k]
+                if p.periodic[k]:
+                    d = (d + 1) % nc[k] - 1
+                if d not in (-1, 0, 1):
+                    ok = False
+            want += ok
+    assert got == want
+    assert got < B.candidate_tests(x, p, nc)
