@@ -111,8 +111,11 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     T phi = T(0);
     int q0, q1, q2;
     cell_coords(cell_s[s], geo, q0, q1, q2);
-    T acc = (FS != 2 && ph.rho_self) ? cw : T(0);
+    // the scan meets the home itself (r = 0, weight w(0)); that term is taken
+    // off at the end unless the self term is asked for
+    T acc = T(0);
     uint32_t cnt = 0;
+    uint32_t* lp = nl + s;                      // next list entry: nl[cnt * cap + s]
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
         if (z < 0) continue;
@@ -130,8 +133,9 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 uint32_t b = start[nc], e = start[nc + 1];
                 if (FS == 1 && !mobile) e = min(max(mend[nc], b), e);     // mobile slots
                 // the common path is one distance test: r_d <= r_c, so the
-                // density term, the list append and the self check all sit
-                // inside the r < r_c branch (about 15 % of the candidates)
+                // density term and the list append sit inside the r < r_c
+                // branch (about 15 % of the candidates); inside it the density
+                // weight is branch-free (zero beyond r_d)
 #pragma unroll 2
                 for (uint32_t j = b; j < e; ++j) {
                     const auto pj = pos4[j];
@@ -139,14 +143,14 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     // (FS = 2 takes frozen candidates only, by type, so it does not
                     // depend on the frozen types the binning ordered by)
-                    if (r2 < rc2 && j != (uint32_t)s &&
-                        (FS != 2 || ((ph.frozen >> unpack_u32(pj.w)) & 1u))) {
-                        if (r2 < rd2) {        // r = 0 (a coincident particle) gives w(0)
-                            const T w = T(1) - sqrt0_t(r2) * inv_rd;
-                            acc += cw * w * w;
-                        }
-                        if (mobile && r2 > T(0)) {
-                            if (cnt < NL_MAX) nl[(int64_t)cnt * cap + s] = (j << 5) | code;
+                    if (r2 < rc2 && (FS != 2 || ((ph.frozen >> unpack_u32(pj.w)) & 1u))) {
+                        const T w = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
+                        acc += cw * w * w;              // r = 0 gives w(0)
+                        if (mobile && r2 > T(0)) {      // not the home, not coincident
+                            if (cnt < NL_MAX) {
+                                *lp = (j << 5) | code;
+                                lp += cap;
+                            }
                             ++cnt;
                             if (want_phi && ((ph.frozen >> unpack_u32(pj.w)) & 1u)) {
                                 const T wq = T(1) - sqrt_t(r2) * inv_rc;
@@ -159,10 +163,11 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
         }
     }
     if constexpr (FS == 2) {
-        rho_ff[id_s[s]] = acc;
+        rho_ff[id_s[s]] = acc;                  // with the home's own w(0)
         return;
     }
     if (FS == 1 && !mobile) acc += rho_ff[id_s[s]];
+    if (!ph.rho_self) acc -= cw;
     rho_out[s] = acc;
     nl_count[s] = cnt;
     if (WANT_PHI) ((T*)ph.phi_out)[s] = phi;
