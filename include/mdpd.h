@@ -250,9 +250,15 @@ int mdpd_pair_count(mdpd_handle* h, int64_t* pairs);
  *   MDPD_OPT_PROFILE_EVERY  m >= 1: with MDPD_OPT_PROFILE on, record the events
  *                      on every m-th step only (default 1), which keeps their
  *                      cost out of most steps.
+ *   MDPD_OPT_DENSITY_SHAPE  0 (default) or 1: code shape of the
+ *                      thread-per-particle density kernel (candidate loop not
+ *                      unrolled, or unrolled by two under a tighter register
+ *                      budget).  Results are identical; only the speed
+ *                      differs (mdpd_autotune picks the faster).
  */
 enum { MDPD_OPT_GRAPH = 1, MDPD_OPT_PROFILE = 2, MDPD_OPT_KERNELS = 3,
-       MDPD_OPT_PROFILE_EVERY = 4, MDPD_OPT_WALL_DENSITY = 5, MDPD_OPT_FORCE_LANES = 6 };
+       MDPD_OPT_PROFILE_EVERY = 4, MDPD_OPT_WALL_DENSITY = 5, MDPD_OPT_FORCE_LANES = 6,
+       MDPD_OPT_DENSITY_SHAPE = 7 };
 enum { MDPD_KERNELS_NLIST = 0, MDPD_KERNELS_SCAN = 1, MDPD_KERNELS_NLIST_THREAD = 2 };
 int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value);
 
@@ -311,14 +317,14 @@ int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double*
  * partners within r_c), CUDA.  Synchronises. */
 int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar);
 
-/* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD)
- * and then the force pass at 1, 2 and 4 lanes per particle
- * (MDPD_OPT_FORCE_LANES; 1 only on a batch) on the current state, reps
- * launches each, and keep the fastest of each.  The trajectory is not
- * advanced.  chosen (may be NULL, 2 ints) receives the density variant and
- * the lanes per particle; ms (may be NULL, 5 doubles) the mean time of each
- * density variant in that order, then of the force pass at 1, 2, 4 lanes
- * (-1: not tried).
+/* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD
+ * in both code shapes of MDPD_OPT_DENSITY_SHAPE) and then the force pass at 1,
+ * 2 and 4 lanes per particle (MDPD_OPT_FORCE_LANES; 1 only on a batch) on the
+ * current state, reps launches each, and keep the fastest of each.  The
+ * trajectory is not advanced.  chosen (may be NULL, 2 ints) receives the
+ * density variant and the lanes per particle; ms (may be NULL, 5 doubles) the
+ * mean time of each density variant in that order (the thread variant's
+ * faster shape), then of the force pass at 1, 2, 4 lanes (-1: not tried).
  * Synchronises. */
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms);
 

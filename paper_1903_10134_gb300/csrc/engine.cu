@@ -85,6 +85,7 @@ struct mdpd_handle {
     bool want_phi = false;
     int kernels = MDPD_KERNELS_NLIST;
     int force_lpp = 1;               // lanes per particle of the force pass (single system)
+    int thread_shape = 0;            // code shape of the thread-per-particle density kernel
     bool walls_set = false;
     std::vector<int32_t> h_type;
     int64_t steps_host = 0;
@@ -471,7 +472,8 @@ void enqueue_density(mdpd_handle* h)
                                       h->start, h->rho, h->nl, h->nl_count);
         else
             launch_density_nl_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
-                                    h->cell_s, h->start, h->rho, h->nl, h->nl_count);
+                                    h->cell_s, h->start, h->rho, h->nl, h->nl_count,
+                                    h->thread_shape);
         return;
     }
     h->ph.phi_out = h->want_phi ? h->phi : nullptr;
@@ -480,7 +482,7 @@ void enqueue_density(mdpd_handle* h)
         // (the wall density is accumulated by this variant only)
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
                           h->cell_s, h->start, h->rho, h->nl, h->nl_count, fs, h->mend,
-                          h->id[h->cur], h->rho_ff);
+                          h->id[h->cur], h->rho_ff, h->thread_shape);
     else if (cell)
         launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph, h->pos4,
                             h->start, h->rho, h->nl, h->nl_count);
@@ -1421,6 +1423,13 @@ int mdpd_set_option(mdpd_handle* h, int32_t option, int64_t value)
         h->force_lpp = (int)value;
         destroy_graphs(h);
         return MDPD_OK;
+    case MDPD_OPT_DENSITY_SHAPE:
+        if (value != 0 && value != 1)
+            return h->fail(MDPD_ERR_INVALID_ARG, "the density code shape is 0 or 1");
+        CK(cudaStreamSynchronize(h->stream));
+        h->thread_shape = (int)value;
+        destroy_graphs(h);
+        return MDPD_OK;
     case MDPD_OPT_WALL_DENSITY:
         if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "a batch has no walls");
         CK(cudaStreamSynchronize(h->stream));
@@ -1606,23 +1615,28 @@ int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
         cudaEventDestroy(e1);
         return code ? h->fail(code, std::string("autotune: ") + what) : MDPD_OK;
     };
-    // 1) density variant
-    const int variants[2] = { MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD };
-    int best = h->kernels;
+    // 1) density variant (the thread-per-particle one in both code shapes;
+    //    ms[1] is its faster shape)
+    const int variants[3] = { MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD,
+                              MDPD_KERNELS_NLIST_THREAD };
+    int best = h->kernels, best_shape = h->thread_shape;
     double best_ms = 1e300;
     enqueue_bin(h, true);                     // same positions: same order, state kept
-    for (int v = 0; v < 2; ++v) {
+    for (int v = 0; v < 3; ++v) {
         h->kernels = variants[v];
+        h->thread_shape = v == 2 ? 1 : 0;
         ensure_ff(h);
         const double t = time_it([&] { enqueue_density(h); });
         if (t < 0) return done(MDPD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-        if (ms) ms[v] = t;
+        if (ms) ms[v < 1 ? 0 : 1] = v == 2 ? std::min(ms[1], t) : t;
         if (t < best_ms) {
             best_ms = t;
             best = variants[v];
+            best_shape = h->thread_shape;
         }
     }
     h->kernels = best;
+    h->thread_shape = best_shape;
     enqueue_density(h);                       // rho and lists from the chosen variant
     // 2) lanes per particle of the force pass (evaluation only: the state is kept)
     const int lanes[3] = { 1, 2, 4 };

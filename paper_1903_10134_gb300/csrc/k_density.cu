@@ -38,8 +38,13 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 // onto the leading lanes, so that warps of frozen homes run the short scans
 // together.  Homes with partner lists (mobile, or every home under list_all)
 // scan everything.
-template <typename T, bool BATCH, bool WANT_PHI, int FS>
-__global__ void __launch_bounds__(PAIR_BLOCK, 12)
+//
+// Two code shapes (SH, picked by the autotuner): 0 = candidate loop not
+// unrolled, registers as the compiler likes (faster on the porous rock);
+// 1 = unrolled by two with at least 8 resident blocks (faster on the batch of
+// slabs).  Their results are identical.
+template <typename T, bool BATCH, bool WANT_PHI, int FS, int SH>
+__global__ void __launch_bounds__(PAIR_BLOCK, SH ? 8 : 12)
 k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
              const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
              const uint32_t* __restrict__ start, T* __restrict__ rho_out,
@@ -136,7 +141,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 // density term and the list append sit inside the r < r_c
                 // branch (about 15 % of the candidates); inside it the density
                 // weight is branch-free (zero beyond r_d)
-#pragma unroll 2
+#pragma unroll(SH ? 2 : 1)
                 for (uint32_t j = b; j < e; ++j) {
                     const auto pj = pos4[j];
                     const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;
@@ -144,7 +149,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                     // (FS = 2 takes frozen candidates only, by type, so it does not
                     // depend on the frozen types the binning ordered by)
                     if (r2 < rc2 && (FS != 2 || ((ph.frozen >> unpack_u32(pj.w)) & 1u))) {
-                        const T w = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
+                        const T w = max(T(1) - sqrt_fast(r2) * inv_rd, T(0));
                         acc += cw * w * w;              // r = 0 gives w(0)
                         if (mobile && r2 > T(0)) {      // not the home, not coincident
                             if (cnt < NL_MAX) {
@@ -286,7 +291,7 @@ __device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, cons
                     const T r2 = dx * dx + dy * dy + dz * dz;
                     // branch-free weight; the home particle's own r = 0 term is
                     // removed after the loop
-                    const T wr = max(T(1) - sqrt0_t(r2) * inv_rd, T(0));
+                    const T wr = max(T(1) - sqrt_fast(r2) * inv_rd, T(0));
                     acc[i] += cw * wr * wr;
                     if ((mobmask >> i) & 1u) {
                         const bool hc = r2 < rc2 && r2 > T(0);
@@ -357,7 +362,7 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
 
 }  // namespace
 
-template <typename T>
+template <typename T, int SH>
 void density_nl_t(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                   const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho,
                   uint32_t* nl, uint32_t* nl_count, int fs, const uint32_t* mend,
@@ -366,9 +371,9 @@ void density_nl_t(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phy
     using V = typename Vec4<T>::type;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
     const bool phi = ph.phi_out != nullptr;
-    auto k = phi ? k_density_nl<T, false, true, 0> : k_density_nl<T, false, false, 0>;
-    if (fs == 1) k = phi ? k_density_nl<T, false, true, 1> : k_density_nl<T, false, false, 1>;
-    if (fs == 2) k = k_density_nl<T, false, false, 2>;
+    auto k = phi ? k_density_nl<T, false, true, 0, SH> : k_density_nl<T, false, false, 0, SH>;
+    if (fs == 1) k = phi ? k_density_nl<T, false, true, 1, SH> : k_density_nl<T, false, false, 1, SH>;
+    if (fs == 2) k = k_density_nl<T, false, false, 2, SH>;
     launch_pdl(k, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const V*)pos4, cell_s,
                start, (T*)rho, nl, nl_count, mend, id_s, (T*)rho_ff);
 }
@@ -376,31 +381,30 @@ void density_nl_t(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phy
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
                        const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
-                       int fs, const uint32_t* mend, const uint32_t* id_s, void* rho_ff)
+                       int fs, const uint32_t* mend, const uint32_t* id_s, void* rho_ff, int shape)
 {
     if (n <= 0) return;
-    if (precision == 0)
-        density_nl_t<double>(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend,
-                             id_s, rho_ff);
-    else
-        density_nl_t<float>(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend,
-                            id_s, rho_ff);
+    auto f = precision == 0 ? (shape ? density_nl_t<double, 1> : density_nl_t<double, 0>)
+                            : (shape ? density_nl_t<float, 1> : density_nl_t<float, 0>);
+    f(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend, id_s, rho_ff);
 }
 
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
                              const void* pos4, const uint32_t* cell_s, const uint32_t* start,
-                             void* rho, uint32_t* nl, uint32_t* nl_count)
+                             void* rho, uint32_t* nl, uint32_t* nl_count, int shape)
 {
     if (bt.nchunk <= 0) return;
     const dim3 g(bt.nchunk), b(PAIR_BLOCK);
     if (precision == 0)
-        launch_pdl_smem(k_density_nl<double, true, false, 0>, g, b, REP_SMEM, st, 0, cap, Geo{},
-                        Phys{}, bt, (const D4*)pos4, cell_s, start, (double*)rho, nl, nl_count,
-                        nullptr, nullptr, nullptr);
+        launch_pdl_smem(shape ? k_density_nl<double, true, false, 0, 1>
+                              : k_density_nl<double, true, false, 0, 0>,
+                        g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{}, bt, (const D4*)pos4, cell_s,
+                        start, (double*)rho, nl, nl_count, nullptr, nullptr, nullptr);
     else
-        launch_pdl_smem(k_density_nl<float, true, false, 0>, g, b, REP_SMEM, st, 0, cap, Geo{},
-                        Phys{}, bt, (const float4*)pos4, cell_s, start, (float*)rho, nl, nl_count,
-                        nullptr, nullptr, nullptr);
+        launch_pdl_smem(shape ? k_density_nl<float, true, false, 0, 1>
+                              : k_density_nl<float, true, false, 0, 0>,
+                        g, b, REP_SMEM, st, 0, cap, Geo{}, Phys{}, bt, (const float4*)pos4, cell_s,
+                        start, (float*)rho, nl, nl_count, nullptr, nullptr, nullptr);
 }
 
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,

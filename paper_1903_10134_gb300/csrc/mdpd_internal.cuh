@@ -284,7 +284,7 @@ void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
                        const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
                        int fs = 0, const uint32_t* mend = nullptr, const uint32_t* id_s = nullptr,
-                       void* rho_ff = nullptr);
+                       void* rho_ff = nullptr, int shape = 0);
 // Warp-per-cell variant of launch_density_nl (same outputs).
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
                          const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,
@@ -314,9 +314,10 @@ void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, c
 void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
                             bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
                             uint32_t* status);
+// shape: code shape of the thread-per-particle kernel (0 or 1; same results).
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
                              const void* pos4, const uint32_t* cell_s, const uint32_t* start,
-                             void* rho, uint32_t* nl, uint32_t* nl_count);
+                             void* rho, uint32_t* nl, uint32_t* nl_count, int shape = 0);
 void launch_density_cell_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
                                const void* pos4, const uint32_t* start, void* rho, uint32_t* nl,
                                uint32_t* nl_count);

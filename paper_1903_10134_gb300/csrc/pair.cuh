@@ -23,6 +23,16 @@ __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 // Same for r^2 >= 0, giving 0 at 0.
 __device__ __forceinline__ float sqrt0_t(float x) { return x * rsqrtf(fmaxf(x, 1e-30f)); }
 __device__ __forceinline__ double sqrt0_t(double x) { return sqrt(x); }
+// r from r^2 >= 0 in one instruction: the PTX approximate square root (its
+// FP32 error is within the density pass's FP32 tolerance; the density parity
+// tests bound it), FP64 correctly rounded.
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double sqrt_fast(double x) { return sqrt(x); }
 
 template <typename T>
 __device__ __forceinline__ T xi_of(U4 w, int dist)

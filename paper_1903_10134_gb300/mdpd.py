@@ -26,6 +26,7 @@ OPT_KERNELS = 3
 OPT_PROFILE_EVERY = 4
 OPT_WALL_DENSITY = 5
 OPT_FORCE_LANES = 6
+OPT_DENSITY_SHAPE = 7
 KERNELS_NLIST = 0
 KERNELS_SCAN = 1
 KERNELS_NLIST_THREAD = 2

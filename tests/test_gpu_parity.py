@@ -492,3 +492,29 @@ def test_frozen_split_graph_direct_and_resume_bitwise(M, precision):
     assert np.array_equal(xa, xc) and np.array_equal(va, vc) and np.array_equal(ra, rc)
     for s in (a, b, c):
         s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("name", ["rock", "tiny"])
+def test_density_code_shapes_agree_bitwise(M, name, precision):
+    """The two code shapes of the thread-per-particle density kernel compute
+    the same arithmetic: trajectories agree bit for bit."""
+    if name == "rock":
+        w, a = _rock_thread(M, precision)
+        _, b = _rock_thread(M, precision)
+    else:
+        w = I.tiny(3000, (8.0, 7.0, 7.5), 41, ntypes=2, g=(0.02, 0.0, 0.0))
+        a, _ = make(M, w, precision)
+        b, _ = make(M, w, precision)
+        for s in (a, b):
+            s.set_option(M.OPT_KERNELS, M.KERNELS_NLIST_THREAD)
+    b.set_option(M.OPT_DENSITY_SHAPE, 1)
+    with pytest.raises(M.MDPDError):
+        b.set_option(M.OPT_DENSITY_SHAPE, 2)
+    for s in (a, b):
+        s.step(12)
+    xa, va, _, ra = a.state()
+    xb, vb, _, rb = b.state()
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+    a.close()
+    b.close()
