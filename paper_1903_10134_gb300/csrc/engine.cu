@@ -1133,6 +1133,16 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
         int ex = 0;
         h->mk.inv_voxel_exact = std::frexp(voxel, &ex) == 0.5 ? 1 : 0;
     }
+    // FP32 voxel index: the FP32 error in voxels is at most about
+    // 4 * 2^-24 * (|x| + |origin|) / voxel, below 5e-4 within these bounds
+    h->mk.fast = 1;
+    for (int k = 0; k < 3; ++k) {
+        const double xmax = std::max(std::fabs(h->geo.lo[k]), std::fabs(h->geo.hi[k]));
+        const double span = (xmax + std::fabs(origin[k])) / voxel;
+        if (dim[k] > 1024 || !(span <= 2048.0)) h->mk.fast = 0;
+        h->mk.origin_f[k] = (float)origin[k];
+    }
+    h->mk.inv_voxel_f = (float)(1.0 / voxel);
     h->walls_set = true;
     h->ff_dirty = true;
     destroy_graphs(h);

@@ -53,7 +53,7 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
         // face, where FP32 rounding could pick the neighbour (on the axes
         // fill_derived marks, the FP32 error is below 4e-4 edges), so the
         // result is always the FP64 one
-        const float t = ((float)xk - ph.df.lo[k]) * ph.df.inv_h[k];
+        const float t = (to_f32(xk) - ph.df.lo[k]) * ph.df.inv_h[k];
         if (!isfinite(t)) {
             st |= ST_NONFINITE;
             q[k] = 0;
@@ -282,13 +282,23 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     cell_s[s] = c;
     // offset from the cell centre lo + (q + 1/2) h, taken in FP64 (the
     // centre as one fused multiply-add on the host-made lo + h/2)
+    // (FP32: no FP64 instruction, see cell_offset_f32; FP64: one fused
+    // multiply-add and one subtraction)
     T off[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-        off[k] = (T)(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
+    for (int k = 0; k < 3; ++k) {
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {
+            const Derived<float>& f = ph_g.df;
+            float o;
+            done = cell_offset_f32(xv[k], q[k], f.h[k], f.h_lo[k], f.c0[k], f.c0_lo[k], &o);
+            off[k] = o;
+        }
+        if (!done) off[k] = to_t<T>(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
+    }
     pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
     // the random stream is keyed on ids within the replica
-    vel4[s] = make4((T)vv[0], (T)vv[1], (T)vv[2], pack_u32(T(0), pid - id0));
+    vel4[s] = make4(to_t<T>(vv[0]), to_t<T>(vv[1]), to_t<T>(vv[2]), pack_u32(T(0), pid - id0));
 }
 
 // Load a state given in id order (pos/vel interleaved xyz) into the master

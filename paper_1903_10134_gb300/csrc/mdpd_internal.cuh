@@ -44,6 +44,8 @@ struct Derived {
     T lo[3];         // box origin
     T inv_h[3];      // 1 / cell edge
     T c0[3];         // centre of cell 0: lo + h / 2
+    T h_lo[3];       // FP32: h - h, c0 - c0 in FP64, rounded (h, c0 as FP32 pairs);
+    T c0_lo[3];      //   FP64: zero
 };
 
 // Physical constants of Sec. 2.1 / Eq. 1, tables flattened [ti * 8 + tj].
@@ -111,6 +113,10 @@ inline void fill_derived(Phys& ph, const Geo& geo)
         f.lo[k] = (float)d.lo[k];
         f.inv_h[k] = (float)d.inv_h[k];
         f.c0[k] = (float)d.c0[k];
+        f.h_lo[k] = (float)(d.h[k] - (double)f.h[k]);
+        f.c0_lo[k] = (float)(d.c0[k] - (double)f.c0[k]);
+        d.h_lo[k] = 0.0;
+        d.c0_lo[k] = 0.0;
     }
 }
 
@@ -151,6 +157,11 @@ struct MaskDev {
     double inv_voxel;      // 1 / voxel
     int inv_voxel_exact;   // voxel is a power of two: t * inv_voxel == t / voxel
     double origin[3];
+    // FP32 voxel index (see drift_reflect): allowed when the mask and the box
+    // span at most 1024 voxels per axis and 2048 voxels from coordinate 0
+    int fast;
+    float origin_f[3];
+    float inv_voxel_f;
 };
 
 // Master particle state, component-major: x[k * cap + i].

@@ -4,6 +4,7 @@
 // observables.
 #pragma once
 
+#include "f64bits.cuh"
 #include "mdpd_internal.cuh"
 #include "philox.cuh"
 #include "vec.cuh"
@@ -126,6 +127,18 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
         int64_t q[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
+            // voxel index in FP32 when that cannot differ from the FP64 one
+            // (mk.fast: FP32 error below 4e-4 voxels; the index is taken only
+            // 2e-3 voxels or more from a face), in FP64 otherwise
+            if (mk.fast) {
+                const float t = (to_f32(xn[k]) - mk.origin_f[k]) * mk.inv_voxel_f;
+                const float fl = floorf(t);
+                if (t - fl > 2e-3f && fl + 1.0f - t > 2e-3f) {
+                    if (!(fl >= 0.0f) || fl >= (float)mk.dim[k]) inside = false;
+                    q[k] = inside ? (int64_t)fl : 0;
+                    continue;
+                }
+            }
             const double t = __dsub_rn(xn[k], mk.origin[k]);
             // for a power-of-two voxel t * (1/voxel) is exactly t / voxel
             const double f = floor(mk.inv_voxel_exact ? __dmul_rn(t, mk.inv_voxel)
@@ -161,7 +174,7 @@ __device__ __forceinline__ void kick_drift_one(int s, int64_t cap, const Geo& ge
     for (int k = 0; k < 3; ++k) {
         x[k] = m.x[k * cap + s];
         const double a = m.a[k * cap + s];
-        const double d = ph.prec32 ? (double)(ph.df.hdt * (float)a) : __dmul_rn(ph.hdt, a);
+        const double d = ph.prec32 ? to_f64(ph.df.hdt * to_f32(a)) : __dmul_rn(ph.hdt, a);
         v[k] = __dadd_rn(m.v[k * cap + s], d);
     }
     drift_reflect(x, v, geo, mk, ph.dt);
@@ -244,24 +257,26 @@ __device__ __forceinline__ void force_finish(int s, bool mobile, const T (&f)[3]
         double v[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) v[k] = m.v[k * cap + s];
+        // (conversions between FP32 and FP64 in integer arithmetic, off the
+        // FP64 pipe: see f64bits.cuh)
         if (MODE == FM_EVAL) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) out[k * cap + s] = (double)af[k];
+            for (int k = 0; k < 3; ++k) out[k * cap + s] = to_f64(af[k]);
         }
         if (mobile) {
             float dv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 dv[k] = MODE == FM_EVAL ? 0.f : dc.hdt * af[k];
-                const float v1 = (float)v[k] + dv[k];          // v(t + dt)
+                const float v1 = to_f32(v[k]) + dv[k];          // v(t + dt)
                 obs[k] = v1;
                 obs[3 + k] = v1 * v1;
             }
             if (MODE == FM_LAST) {
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
-                    m.v[k * cap + s] = __dadd_rn(v[k], (double)dv[k]);
-                    m.a[k * cap + s] = (double)af[k];
+                    m.v[k * cap + s] = __dadd_rn(v[k], to_f64(dv[k]));
+                    m.a[k * cap + s] = to_f64(af[k]);
                 }
             }
             if (MODE == FM_FUSED) {
@@ -271,7 +286,7 @@ __device__ __forceinline__ void force_finish(int s, bool mobile, const T (&f)[3]
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
                     x[k] = m.x[k * cap + s];
-                    const double d = (double)dv[k];
+                    const double d = to_f64(dv[k]);
                     v[k] = __dadd_rn(__dadd_rn(v[k], d), d);
                 }
                 drift_reflect(x, v, geo, mk, ph.dt);
