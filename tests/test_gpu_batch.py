@@ -207,3 +207,30 @@ def test_uneven_batch_sampled_members(M):
     assert np.all(np.isfinite(obs)) and np.all(obs[:, 15] == 30)
     assert np.array_equal(obs[:, 14], ns.astype(float))      # mobile count per replica
     b.close()
+
+
+def test_full_batch_sampled_parity(M):
+    """The full 256-replica batch as the bench runs it (FP32, autotuned, a few
+    steps): for four replicas (smallest, largest, two others) the densities
+    of all their particles and the forces of a sample equal the oracle's at
+    the same state and step index."""
+    import math
+    ws = I.batch_slabs(nrep=256, seed=1, precision=1)
+    b = M.Batch.from_workloads(ws)
+    b.autotune()
+    b.step(5)
+    f, rho = b.forces()
+    x, v, t, _ = b.state()
+    ns = np.array([w.n for w in ws])
+    for r in (int(ns.argmin()), int(ns.argmax()), 77, 200):
+        a0, a1 = b.offsets[r], b.offsets[r + 1]
+        w = ws[r]
+        o = O.Oracle(w.params.copy(precision=0), x[a0:a1], v[a0:a1], t[a0:a1], w.seed,
+                     use_cells=True)
+        assert np.abs(rho[a0:a1] - o.rho).max() <= 2e-6 * o.rho.max(), r
+        idx = np.random.default_rng(r).choice(a1 - a0, min(200, a1 - a0), replace=False)
+        ref = o.forces_subset(idx, rho=o.rho, step=5)
+        rms = math.sqrt(np.mean(np.sum(ref ** 2, axis=1)))
+        err = np.linalg.norm(f[a0:a1][idx] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
+        assert err.max() <= 1e-5, (r, err.max())
+    b.close()

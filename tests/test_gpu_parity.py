@@ -518,3 +518,32 @@ def test_density_code_shapes_agree_bitwise(M, name, precision):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("name", ["rock", "slit"])
+def test_full_walled_workload_sampled_parity(M, name):
+    """The full-size walled workloads as the bench runs them (FP32, kernels
+    picked by the autotuner, frozen split on, a few fused steps): after the
+    steps, the densities of all particles (fluid and wall) and the forces of
+    a sample of 400 fluid particles at the current step index equal the
+    oracle's at the same state."""
+    w = I.rock() if name == "rock" else I.slit()
+    s = M.System.from_workload(w, precision=1)
+    s.autotune()
+    s.step(5)
+    x, v, t, rho = s.state()
+    k = M.mdpd_step_count(s.h)
+    assert k == 5
+    f, rho_e = s.forces()                     # evaluation at the current state, step index k
+    assert np.array_equal(rho, rho_e)
+    p = w.params.copy(precision=0)
+    o = O.Oracle(p, x, v, t, w.seed, use_cells=True)
+    assert np.abs(rho - o.rho).max() <= RHO_TOL[1] * o.rho.max()
+    mobile = np.flatnonzero(t != w.wall_type)
+    idx = np.random.default_rng(1).choice(mobile, 400, replace=False)
+    ref = o.forces_subset(idx, rho=o.rho, step=k)
+    rms = math.sqrt(np.mean(np.sum(ref ** 2, axis=1)))
+    err = np.linalg.norm(f[idx] - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), rms)
+    assert err.max() <= TOL[1], err.max()
+    assert np.all(f[t == w.wall_type] == 0)
+    s.close()
