@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "mdpd_internal.cuh"
+#include "philox.cuh"
 #include "vec.cuh"
 
 using namespace mdpd;
@@ -353,6 +354,7 @@ void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
     f.prec32 = p.precision == 1 ? 1 : 0;
     f.key0 = (uint32_t)seed;
     f.key1 = (uint32_t)(seed >> 32);
+    philox_round_keys(f.key0, f.key1, f.rk);
     for (int a = 0; a < 8; ++a)
         for (int b = 0; b < 8; ++b) {
             f.A[a * 8 + b] = p.A[a][b];
@@ -1005,6 +1007,7 @@ int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params)
         make_geo_phys(params[r], 0, g, R.ph);
         R.ph.key0 = k0;
         R.ph.key1 = k1;
+        philox_round_keys(k0, k1, R.ph.rk);
         h->rep_p[r] = params[r];
     }
     // the records live in device memory: captured graphs stay valid

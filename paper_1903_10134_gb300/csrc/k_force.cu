@@ -59,7 +59,7 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
     static_assert(!BATCH || LPP == 1, "a batch chunk is one particle per lane");
     constexpr int PPB = PAIR_BLOCK / LPP;        // particles per block
     __shared__ PairTables<T> tab;
-    __shared__ T shift[27][3];
+    __shared__ V shift[27];                      // image shift of neighbour-cell code (xyz)
     __shared__ int act[PAIR_BLOCK];
     __shared__ int wsum[PAIR_BLOCK / 32];
     int s0;
@@ -84,9 +84,8 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
     if (threadIdx.x < 27) {
         const int c = threadIdx.x;
         const Derived<T>& dc = derived<T>(ph);
-        shift[c][0] = (T)(c % 3 - 1) * dc.h[0];
-        shift[c][1] = (T)((c / 3) % 3 - 1) * dc.h[1];
-        shift[c][2] = (T)(c / 9 - 1) * dc.h[2];
+        shift[c] = make4((T)(c % 3 - 1) * dc.h[0], (T)((c / 3) % 3 - 1) * dc.h[1],
+                         (T)(c / 9 - 1) * dc.h[2], T(0));
     }
     // compact the block's mobile particles onto the first lanes, in cell order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -124,10 +123,7 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
         const T rho_i = rho[s];
         const uint32_t ti = unpack_u32(pi.w);
         const uint32_t id_i = unpack_u32(vi.w);
-        const T* tA = tab.A + ti * 8;
-        const T* tB = tab.B + ti * 8;
-        const T* tG = tab.G + ti * 8;
-        const T* tS = tab.S + ti * 8;
+        const V* tP = tab.P + ti * 8;
         const uint32_t cnt = nl_count[s];
         if (cnt <= (uint32_t)NL_MAX) {
             const uint32_t k0 = (uint32_t)sub;
@@ -141,13 +137,13 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                 const V pn = pos4[e1 >> 5];
                 const V vn = vel4[e1 >> 5];
                 const T rn = rho[e1 >> 5];
-                const uint32_t code = e0 & 31u;
-                const T dx = pi.x - shift[code][0] - pj.x;
-                const T dy = pi.y - shift[code][1] - pj.y;
-                const T dz = pi.z - shift[code][2] - pj.z;
+                const V sh = shift[e0 & 31u];
+                const T dx = pi.x - sh.x - pj.x;
+                const T dy = pi.y - sh.y - pj.y;
+                const T dz = pi.z - sh.z - pj.z;
                 const T r2 = dx * dx + dy * dy + dz * dz;
-                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i, rj,
-                          unpack_u32(pj.w), id_i, unpack_u32(vj.w), step, ph, f, W);
+                pair_term<T, !BATCH>(c, tP[unpack_u32(pj.w)], dx, dy, dz, r2, vi, vj, rho_i, rj,
+                                     id_i, unpack_u32(vj.w), step, ph, f, W);
                 e0 = e1;
                 e1 = e2;
                 pj = pn;
@@ -173,15 +169,16 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                         const uint32_t b = start[nc], e = start[nc + 1];
                         for (uint32_t j = b; j < e; ++j) {
                             const V pj = pos4[j];
-                            const T dx = pi.x - shift[code][0] - pj.x;
-                            const T dy = pi.y - shift[code][1] - pj.y;
-                            const T dz = pi.z - shift[code][2] - pj.z;
+                            const V sh = shift[code];
+                            const T dx = pi.x - sh.x - pj.x;
+                            const T dy = pi.y - sh.y - pj.y;
+                            const T dz = pi.z - sh.z - pj.z;
                             const T r2 = dx * dx + dy * dy + dz * dz;
                             if (r2 < c.rc2 && r2 > T(0)) {
                                 const V vj = vel4[j];
-                                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i,
-                                          rho[j], unpack_u32(pj.w), id_i, unpack_u32(vj.w),
-                                          step, ph, f, W);
+                                pair_term<T, !BATCH>(c, tP[unpack_u32(pj.w)], dx, dy, dz, r2, vi,
+                                                     vj, rho_i, rho[j], id_i, unpack_u32(vj.w),
+                                                     step, ph, f, W);
                                 ++npair;
                             }
                         }

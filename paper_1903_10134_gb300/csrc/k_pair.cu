@@ -106,10 +106,7 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
         if (mobile) {
             int q0, q1, q2;
             cell_coords(cell_s[s], geo, q0, q1, q2);
-            const T* tA = tab.A + ti * 8;
-            const T* tB = tab.B + ti * 8;
-            const T* tG = tab.G + ti * 8;
-            const T* tS = tab.S + ti * 8;
+            const auto* tP = tab.P + ti * 8;
             for (int oz = -1; oz <= 1; ++oz) {
                 const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
                 if (z < 0) continue;
@@ -130,8 +127,9 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
                             const T r2 = dx * dx + dy * dy + dz * dz;
                             if (r2 < c.rc2 && r2 > T(0)) {
                                 const auto vj = vel4[j];
-                                pair_term(c, tA, tB, tG, tS, dx, dy, dz, r2, vi, vj, rho_i, rho[j],
-                                          unpack_u32(pj.w), id_i, unpack_u32(vj.w), step, ph, f, W);
+                                pair_term<T, true>(c, tP[unpack_u32(pj.w)], dx, dy, dz, r2, vi, vj,
+                                                   rho_i, rho[j], id_i, unpack_u32(vj.w), step,
+                                                   ph, f, W);
                                 ++npair;
                             }
                         }

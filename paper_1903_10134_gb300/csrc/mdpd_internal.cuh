@@ -61,6 +61,7 @@ struct Phys {
     uint32_t fast_cell;           // bit k: axis k may take cell indices in FP32 (see k_bin_count)
     void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
+    uint32_t rk[10][2];           // its ten round keys (key + r * Weyl increments; set_keys)
     Derived<float> df;
     Derived<double> dd;
     double A[64], B[64], gamma[64], sigma[64];   // keep last: a batch copies what precedes A

@@ -46,18 +46,14 @@ __device__ __forceinline__ T xi_of(U4 w, int dist)
 // Per-type-pair tables in shared memory, row ti: A, B, gamma, sigma.
 template <typename T>
 struct PairTables {
-    T A[64], B[64], G[64], S[64];
+    typename Vec4<T>::type P[64];     // (A, B, gamma, sigma) of type pair [ti * 8 + tj]
 };
 
 template <typename T>
 __device__ __forceinline__ void load_tables(PairTables<T>& t, const Phys& ph)
 {
-    for (int k = threadIdx.x; k < 64; k += blockDim.x) {
-        t.A[k] = (T)ph.A[k];
-        t.B[k] = (T)ph.B[k];
-        t.G[k] = (T)ph.gamma[k];
-        t.S[k] = (T)ph.sigma[k];
-    }
+    for (int k = threadIdx.x; k < 64; k += blockDim.x)
+        t.P[k] = make4((T)ph.A[k], (T)ph.B[k], (T)ph.gamma[k], (T)ph.sigma[k]);
 }
 
 template <typename T>
@@ -74,22 +70,23 @@ struct PairConst {
 // the conservative virial 0.5 d_a F^C e_b to W:
 //   F = [A w_C + B (rho_i + rho_j) w_d [r < r_d] - gamma w_C^2 (e.v_ij)
 //        + sigma w_C xi_ij / sqrt(dt)] e,   w_C = 1 - r/r_c, w_d = 1 - r/r_d.
-template <typename T, typename V4>
-__device__ __forceinline__ void pair_term(const PairConst<T>& c, const T* tA, const T* tB,
-                                          const T* tG, const T* tS, T dx, T dy, T dz, T r2,
-                                          const V4& vi, const V4& vj, T rho_i, T rho_j,
-                                          uint32_t tj, uint32_t id_i, uint32_t id_j,
-                                          uint64_t step, const Phys& ph, T (&f)[3], T (&W)[6])
+template <typename T, bool RK, typename V4>
+__device__ __forceinline__ void pair_term(const PairConst<T>& c, const V4& prm, T dx, T dy, T dz,
+                                          T r2, const V4& vi, const V4& vj, T rho_i, T rho_j,
+                                          uint32_t id_i, uint32_t id_j, uint64_t step,
+                                          const Phys& ph, T (&f)[3], T (&W)[6])
 {
+    // prm = (A, B, gamma, sigma) of the pair's types
     const T rinv = rsqrt_t(r2);
     const T r = r2 * rinv;
     const T wc = T(1) - r * c.inv_rc;
-    T fc = tA[tj] * wc;
-    if (r2 < c.rd2) fc += tB[tj] * (rho_i + rho_j) * (T(1) - r * c.inv_rd);
+    T fc = prm.x * wc;
+    if (r2 < c.rd2) fc += prm.y * (rho_i + rho_j) * (T(1) - r * c.inv_rd);
     const T ev = (dx * (vi.x - vj.x) + dy * (vi.y - vj.y) + dz * (vi.z - vj.z)) * rinv;
-    const T fd = -tG[tj] * wc * wc * ev;
-    const U4 w = pair_draw(id_i, id_j, step, ph.key0, ph.key1);
-    const T fr = tS[tj] * wc * xi_of<T>(w, ph.xi_dist) * c.inv_sqrt_dt;
+    const T fd = -prm.z * wc * wc * ev;
+    const U4 w = RK ? pair_draw_rk(id_i, id_j, step, ph.rk)
+                    : pair_draw(id_i, id_j, step, ph.key0, ph.key1);
+    const T fr = prm.w * wc * xi_of<T>(w, ph.xi_dist) * c.inv_sqrt_dt;
     const T fp = (fc + fd + fr) * rinv;
     f[0] += fp * dx;
     f[1] += fp * dy;

@@ -35,6 +35,36 @@ __device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1)
     return c;
 }
 
+// The same rounds with the round keys given (rk[r] = key + r * increments,
+// prepared on the host): in a kernel whose Phys is a launch parameter the
+// keys are read as constant operands, with no additions per round.
+__device__ __forceinline__ U4 philox4x32_10_rk(U4 c, const uint32_t (&rk)[10][2])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        U4 n;
+        n.x = hi1 ^ c.y ^ rk[r][0];
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ rk[r][1];
+        n.w = lo0;
+        c = n;
+    }
+    return c;
+}
+
+// Round keys of the key (k0, k1), as philox4x32_10 forms them.
+inline void philox_round_keys(uint32_t k0, uint32_t k1, uint32_t (&rk)[10][2])
+{
+    for (int r = 0; r < 10; ++r) {
+        rk[r][0] = k0 + (uint32_t)r * 0x9E3779B9u;
+        rk[r][1] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
+}
+
 // Word 0 of the pair draw for the force evaluation of `step`; the counter
 // holds (min id, max id, step) so both members of a pair see the same value.
 __device__ __forceinline__ U4 pair_draw(uint32_t id_i, uint32_t id_j, uint64_t step,
@@ -46,6 +76,17 @@ __device__ __forceinline__ U4 pair_draw(uint32_t id_i, uint32_t id_j, uint64_t s
     c.z = (uint32_t)step;
     c.w = (uint32_t)(step >> 32);
     return philox4x32_10(c, k0, k1);
+}
+
+__device__ __forceinline__ U4 pair_draw_rk(uint32_t id_i, uint32_t id_j, uint64_t step,
+                                           const uint32_t (&rk)[10][2])
+{
+    U4 c;
+    c.x = min(id_i, id_j);
+    c.y = max(id_i, id_j);
+    c.z = (uint32_t)step;
+    c.w = (uint32_t)(step >> 32);
+    return philox4x32_10_rk(c, rk);
 }
 
 // Uniform xi with zero mean and unit variance: sqrt(3) * m * 2^-24 with the odd
