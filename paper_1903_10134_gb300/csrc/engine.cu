@@ -10,6 +10,7 @@
 #include <utility>
 #include <vector>
 
+#include "f64bits.cuh"
 #include "mdpd_internal.cuh"
 #include "philox.cuh"
 #include "vec.cuh"
@@ -337,6 +338,8 @@ void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
         g.lo[k] = p.box_lo[k];
         g.L[k] = p.box[k];
         g.hi[k] = p.box_lo[k] + p.box[k];
+        g.key_lo[k] = f64_key(g.lo[k]);
+        g.key_hi[k] = f64_key(g.hi[k]);
         g.h[k] = p.box[k] / m;
         g.inv_h[k] = 1.0 / g.h[k];
         g.ncell *= m;

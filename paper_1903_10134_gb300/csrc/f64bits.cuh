@@ -132,6 +132,16 @@ MDPD_HD bool cell_offset_f32(double x, int q, float h_hi, float h_lo, float c0_h
     return true;
 }
 
+// A signed 64-bit key that orders binary64 values as their comparison does
+// (for everything but NaN; -0 and +0 get the same key): x < y exactly when
+// f64_key(x) < f64_key(y).
+MDPD_HD int64_t f64_key(double x)
+{
+    const int64_t b = (int64_t)f64_bits(x);
+    if (b == (int64_t)0x8000000000000000ull) return 0;          // -0 orders as +0
+    return b >= 0 ? b : (b ^ (int64_t)0x7FFFFFFFFFFFFFFFull);
+}
+
 MDPD_HD int clz32(uint32_t v)
 {
 #if defined(__CUDA_ARCH__)

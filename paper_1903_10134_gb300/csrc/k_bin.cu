@@ -285,16 +285,21 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     // (FP32: no FP64 instruction, see cell_offset_f32; FP64: one fused
     // multiply-add and one subtraction)
     T off[3];
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        const Derived<float>& f = ph_g.df;
+        done = true;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        bool done = false;
-        if constexpr (sizeof(T) == 4) {
-            const Derived<float>& f = ph_g.df;
+        for (int k = 0; k < 3; ++k) {
             float o;
-            done = cell_offset_f32(xv[k], q[k], f.h[k], f.h_lo[k], f.c0[k], f.c0_lo[k], &o);
+            done &= cell_offset_f32(xv[k], q[k], f.h[k], f.h_lo[k], f.c0[k], f.c0_lo[k], &o);
             off[k] = o;
         }
-        if (!done) off[k] = to_t<T>(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
+    }
+    if (!done) {            // FP64 pairs, or a coordinate outside the FP32 split's range
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            off[k] = to_t<T>(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
     }
     pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
     // the random stream is keyed on ids within the replica

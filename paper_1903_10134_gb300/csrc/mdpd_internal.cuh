@@ -25,6 +25,7 @@ struct Geo {
     int nc[3];
     int periodic[3];
     double lo[3], L[3], hi[3], h[3], inv_h[3];
+    int64_t key_lo[3], key_hi[3];   // f64_key(lo), f64_key(hi): face comparisons in integers
     int64_t ncell;
 };
 

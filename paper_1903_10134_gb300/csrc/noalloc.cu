@@ -23,6 +23,7 @@
 #include <mutex>
 #include <string>
 
+#include "f64bits.cuh"
 #include "mdpd_internal.cuh"
 #include "vec.cuh"
 
@@ -183,6 +184,8 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
         geo.lo[k] = p->box_lo[k];
         geo.L[k] = p->box[k];
         geo.hi[k] = p->box_lo[k] + p->box[k];
+        geo.key_lo[k] = f64_key(geo.lo[k]);
+        geo.key_hi[k] = f64_key(geo.hi[k]);
         geo.h[k] = p->box[k] / m;
         geo.inv_h[k] = 1.0 / geo.h[k];
         geo.ncell *= m;

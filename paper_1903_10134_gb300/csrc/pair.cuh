@@ -112,10 +112,13 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         xn[k] = __dadd_rn(x[k], __dmul_rn(dt, v[k]));
+        // the comparisons with the box faces on integer keys of the bits
+        // (f64_key orders like the FP64 comparison, off the FP64 pipe)
+        const int64_t kx = f64_key(xn[k]);
         if (geo.periodic[k]) {
-            if (xn[k] >= geo.hi[k]) xn[k] = __dsub_rn(xn[k], geo.L[k]);
-            else if (xn[k] < geo.lo[k]) xn[k] = __dadd_rn(xn[k], geo.L[k]);
-        } else if (xn[k] < geo.lo[k] || xn[k] >= geo.hi[k]) {
+            if (kx >= geo.key_hi[k]) xn[k] = __dsub_rn(xn[k], geo.L[k]);
+            else if (kx < geo.key_lo[k]) xn[k] = __dadd_rn(xn[k], geo.L[k]);
+        } else if (kx < geo.key_lo[k] || kx >= geo.key_hi[k]) {
             blocked = true;
         }
     }

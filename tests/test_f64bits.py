@@ -82,6 +82,19 @@ int main() {
         const double d = f32_to_f64(x, &ok);
         if (!ok || f64_bits(d) != f64_bits((double)x)) { std::printf("ZERO\n"); ++bad; }
     }
+    // order keys against the comparison operators (random values, both zeros,
+    // infinities, neighbours of each other)
+    for (int i = 0; i < 2000000; ++i) {
+        double a = bits_f64(rng()), b2 = (i & 1) ? std::nextafter(a, (i & 2) ? 1e308 : -1e308)
+                                                 : bits_f64(rng());
+        if (std::isnan(a) || std::isnan(b2)) continue;
+        if ((f64_key(a) < f64_key(b2)) != (a < b2) || (f64_key(a) >= f64_key(b2)) != (a >= b2)) {
+            std::printf("KEY %.17g %.17g\n", a, b2); ++bad;
+        }
+    }
+    const double kz[] = {0.0, -0.0, 1e-310, -1e-310, INFINITY, -INFINITY, 1.0, -1.0};
+    for (double a : kz) for (double b2 : kz)
+        if ((f64_key(a) < f64_key(b2)) != (a < b2)) { std::printf("KEYZ %g %g\n", a, b2); ++bad; }
     // integers to binary64
     for (int i = 0; i < 2000000; ++i) {
         const uint32_t q = (uint32_t)(rng() >> (rng() % 64));
