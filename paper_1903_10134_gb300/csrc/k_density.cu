@@ -188,6 +188,10 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
 // shared memory, then written slot-major (nl[k * cap + i]).
 constexpr int DC_WARPS = 4;
 constexpr int DC_GROUP = 8;
+// Candidate sequences up to this length get a table from candidate position
+// to neighbour cell, built once per home cell; longer ones (dense regions)
+// search the cells' prefix sums instead.
+constexpr int DC_MAP = 384;
 
 // The work of one warp on home cell c (global index; cell0 = first cell of
 // its replica).  Shared memory is per warp (index w).
@@ -206,6 +210,8 @@ __device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, cons
     __shared__ uint32_t cbase[DC_WARPS][27];
     __shared__ uint32_t ccnt[DC_WARPS][DC_GROUP];
     __shared__ uint32_t lst[DC_WARPS][NL_MAX][DC_GROUP];
+    __shared__ uint8_t cellmap[DC_WARPS][DC_MAP];
+    __shared__ V cshift[DC_WARPS][27];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t hb = start[c], he = start[c + 1];
     if (hb == he) return;                         // whole warp: empty cell
@@ -229,19 +235,23 @@ __device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, cons
         if (lane >= o) inc += t;
     }
     const uint32_t C = __shfl_sync(0xffffffffu, inc, 31);
-    if (lane < 27) {
-        pre[w][lane] = inc - cn;
-        cbase[w][lane] = cb;
-    }
-    if (lane == 27) pre[w][27] = C;
-    __syncwarp();
-
     const Derived<T>& dc = derived<T>(ph);
     const T rc2 = dc.rc2;
     const T inv_rd = dc.inv_rd;
     const T cw = dc.cw_rho;
-    const T hx = dc.h[0], hy = dc.h[1], hz = dc.h[2];
     const unsigned lt = (1u << lane) - 1u;
+    const bool use_map = C <= (uint32_t)DC_MAP;   // warp-uniform
+    if (lane < 27) {
+        pre[w][lane] = inc - cn;
+        cbase[w][lane] = cb;
+        // the neighbour cell's image shift into the home cell's frame
+        cshift[w][lane] = make4((T)(lane % 3 - 1) * dc.h[0], (T)((lane / 3) % 3 - 1) * dc.h[1],
+                                (T)(lane / 9 - 1) * dc.h[2], T(0));
+        if (use_map)
+            for (uint32_t t = inc - cn; t < inc; ++t) cellmap[w][t] = (uint8_t)lane;
+    }
+    if (lane == 27) pre[w][27] = C;
+    __syncwarp();
 
     // far-away stand-in for the candidate slots past the end of the last round:
     // beyond r_c and r_d of every home particle, finite in FP32
@@ -267,19 +277,25 @@ __device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, cons
         for (uint32_t t0 = 0; t0 < C; t0 += 32) {
             const uint32_t t = t0 + lane;
             const bool valid = t < C;
-            int lo = 0, hi = 27;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (pre[w][mid] <= t) lo = mid;
-                else hi = mid;
+            int lo = 0;
+            if (use_map) {
+                lo = valid ? (int)cellmap[w][t] : 0;
+            } else {
+                int hi = 27;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (pre[w][mid] <= t) lo = mid;
+                    else hi = mid;
+                }
             }
             const uint32_t j = valid ? cbase[w][lo] + (t - pre[w][lo]) : hb;
             const V pj = pos4[j];
             // the candidate in the home cell's frame (its image across the
             // neighbour cell offset)
-            const T cx = valid ? pj.x + (T)(lo % 3 - 1) * hx : far;
-            const T cy = valid ? pj.y + (T)((lo / 3) % 3 - 1) * hy : far;
-            const T cz = valid ? pj.z + (T)(lo / 9 - 1) * hz : far;
+            const V sh = cshift[w][lo];
+            const T cx = valid ? pj.x + sh.x : far;
+            const T cy = valid ? pj.y + sh.y : far;
+            const T cz = valid ? pj.z + sh.z : far;
             const uint32_t entry = (j << 5) | (uint32_t)lo;
 #pragma unroll
             for (int i = 0; i < DC_GROUP; ++i) {
