@@ -66,6 +66,9 @@ struct mdpd_handle {
     // binning
     uint32_t *count = nullptr, *start = nullptr, *cellof = nullptr, *slot = nullptr;
     uint32_t *key = nullptr, *src = nullptr, *scan_tmp = nullptr;
+    // the scan's per-tile sums of the counts, formed by the count kernel; two
+    // buffers of scan_num_blocks(ncell) words used by binning parity (cur)
+    uint32_t* tile_sums = nullptr;
     uint32_t* mend = nullptr;        // first frozen slot of each cell (see launch_rank_gather)
     // frozen-frozen part of each frozen particle's density, by id (constant
     // while the frozen particles and r_d stay; recomputed when ff_dirty)
@@ -422,15 +425,24 @@ void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
 {
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
-    // count[] is zero here: cleared at creation and by every scan
+    // count[] and this parity's tile sums are zero here: cleared at creation
+    // and by every scan (which clears the other parity's tile sums)
+    const int64_t nb = scan_num_blocks(h->geo.ncell);
+    const bool fused = scan_fused_sums(h->geo.ncell);
+    uint32_t* tsum = fused ? h->tile_sums + (size_t)h->cur * nb : nullptr;
+    uint32_t* tsum_next = h->tile_sums + (size_t)(1 - h->cur) * nb;
     if (h->nrep)
         launch_bin_count_batch(st, h->cap, h->batch(), master(h, h->cur), kick, h->cellof,
-                               h->slot, h->count, h->status);
+                               h->slot, h->count, tsum, h->status);
     else
         launch_bin_count(st, n, h->cap, h->geo, h->ph, h->mk, master(h, h->cur), kick, h->cellof,
-                         h->slot, h->count, h->status);
-    launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp, true);
-    launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src);
+                         h->slot, h->count, tsum, h->status);
+    if (fused)
+        launch_scan_from_sums(st, h->count, h->geo.ncell, h->start, tsum, tsum_next);
+    else
+        launch_exclusive_scan(st, h->count, h->geo.ncell, h->start, h->scan_tmp, true);
+    launch_bin_scatter(st, n, h->cellof, h->slot, h->start, h->id[h->cur], h->key, h->src,
+                       h->status);
     if (h->nrep)
         launch_rank_gather_batch(st, h->precision, h->cap, h->cellof, h->start, h->key, h->src,
                                  master(h, h->cur), master(h, 1 - h->cur), gather_a, h->batch(),
@@ -755,6 +767,7 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
         (rc = dalloc(h, &h->start, (size_t)(h->geo.ncell + 1) * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->mend, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->scan_tmp, (size_t)(nb + 1) * sizeof(uint32_t))) ||
+        (rc = dalloc(h, &h->tile_sums, (size_t)2 * nb * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->status, sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->step, sizeof(uint64_t))) ||
         (rc = dalloc(h, &h->red_ticket, sizeof(unsigned))) ||
@@ -781,6 +794,9 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
               cudaMemsetAsync(h->step, 0, sizeof(uint64_t), st) == cudaSuccess &&
               cudaMemsetAsync(h->red_ticket, 0, sizeof(unsigned), st) == cudaSuccess &&
               cudaMemsetAsync(h->count, 0, (size_t)h->geo.ncell * sizeof(uint32_t), st) == cudaSuccess &&
+              cudaMemsetAsync(h->tile_sums, 0,
+                              (size_t)2 * scan_num_blocks(h->geo.ncell) * sizeof(uint32_t),
+                              st) == cudaSuccess &&
               cudaMemsetAsync(h->obs, 0, (2 * MDPD_NUM_OBS + 2) * sizeof(double), st) == cudaSuccess;
     if (ok && n > 0)
         ok = cudaMemcpyAsync(h->fout, pos, (size_t)n * 3 * sizeof(double), kind, st) == cudaSuccess &&
@@ -1113,6 +1129,11 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
          cudaMemcpyAsync(h->type_by_id, tmpH.type_by_id, (size_t)n_old, cudaMemcpyDeviceToDevice, st) == cudaSuccess &&
          cudaMemsetAsync(h->type_by_id + n_old, wall_type, (size_t)nw, st) == cudaSuccess;
     h->cur = 0;
+    // the scan's tile sums follow the buffer parity: with the parity reset,
+    // clear both so the next binning starts from zero whichever it uses
+    ok = ok && cudaMemsetAsync(h->tile_sums, 0,
+                               (size_t)2 * scan_num_blocks(h->geo.ncell) * sizeof(uint32_t),
+                               st) == cudaSuccess;
     if (ok) {
         launch_wall_emit(st, dmask, dim, cnt, off, voxel, origin, k0, k1, n_old, h->cap,
                          master(h, 0), (uint8_t)wall_type);
@@ -1702,6 +1723,7 @@ void mdpd_destroy(mdpd_handle* h)
     dfree(h->start);
     dfree(h->mend);
     dfree(h->scan_tmp);
+    dfree(h->tile_sums);
     dfree(h->status);
     dfree(h->step);
     dfree(h->red_ticket);

@@ -13,16 +13,26 @@ namespace {
 
 constexpr int BLOCK = 256;
 
+// exclusive scan of the cell counts: tiles of SCAN_TILE cells, one block each
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
 inline unsigned nblocks(int64_t n, int b = BLOCK) { return (unsigned)((n + b - 1) / b); }
 
 // Batched kernels (BATCH = true) take their replica from the chunk of the
 // block (see Batch); single-system kernels index by the global thread id.
 // KICK: first apply the step's first half-kick, drift and reflection to the
 // particle (the work of a separate kick launch at the start of mdpd_step).
+// tsum (or nullptr): the scan's per-tile sums of the counts, added here (one
+// atomic per tile and warp: consecutive particles mostly share a tile), so
+// that the scan needs no launch of its own to form them.  Used for lattices
+// of few tiles; with many, the atomics cost more than the launch they save.
 template <bool BATCH, bool KICK>
 __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                             Master m, uint32_t* __restrict__ cellof, uint32_t* __restrict__ slot,
-                            uint32_t* __restrict__ count, uint32_t* __restrict__ status)
+                            uint32_t* __restrict__ count, uint32_t* __restrict__ tsum,
+                            uint32_t* __restrict__ status)
 {
     pdl_enter();
     int i;
@@ -39,6 +49,7 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
         i = blockIdx.x * blockDim.x + threadIdx.x;
         valid = i < n;
     }
+    const unsigned act = __ballot_sync(0xffffffffu, valid);
     if (!valid) return;
     const Geo& geo = BATCH ? rp->geo : geo_p;
     const Phys& ph = BATCH ? rp->ph : ph_p;
@@ -77,12 +88,15 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
     // frozen particles after its mobile ones)
     const uint32_t fz = (ph.frozen >> m.type[i]) & 1u;
     slot[i] = atomicAdd(&count[c], 1u) | (fz << 31);
+    if (tsum != nullptr) {                     // uniform over the launch
+        const uint32_t tile = c / (uint32_t)SCAN_TILE;
+        const unsigned peers = __match_any_sync(act, tile);
+        if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+            atomicAdd(&tsum[tile], (uint32_t)__popc(peers));
+    }
 }
 
 // ---- exclusive scan ------------------------------------------------------------
-constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_ITEMS = 4;
-constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
 // Exclusive prefix of v over the block; *total receives the block sum.
 __device__ uint32_t block_exclusive(uint32_t v, uint32_t* total)
@@ -136,9 +150,12 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(uint32_t* __restric
                                                              int64_t n,
                                                              const uint32_t* __restrict__ sums,
                                                              int nb, uint32_t* __restrict__ out,
-                                                             int zero_in)
+                                                             int zero_in,
+                                                             uint32_t* __restrict__ zero_sums)
 {
     pdl_enter();
+    // the binning's tile sums alternate between two buffers: clear the other
+    if (zero_sums && threadIdx.x == 0) zero_sums[blockIdx.x] = 0u;
     __shared__ uint32_t before_sh;
     const int b = (int)blockIdx.x;
     uint32_t mine = 0, all = 0;
@@ -176,13 +193,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(uint32_t* __restric
 __global__ void k_bin_scatter(int n, const uint32_t* __restrict__ cellof,
                               const uint32_t* __restrict__ slot, const uint32_t* __restrict__ start,
                               const uint32_t* __restrict__ id, uint32_t* __restrict__ key,
-                              uint32_t* __restrict__ src)
+                              uint32_t* __restrict__ src, uint32_t* __restrict__ status)
 {
     pdl_enter();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t sl = slot[i];
     const uint32_t dst = start[cellof[i]] + (sl & 0x7fffffffu);
+    if (dst >= (uint32_t)n) {          // inconsistent counts: report, write nothing
+        atomicOr(status, ST_OVERFLOW);
+        return;
+    }
     key[dst] = id[i] | (sl & 0x80000000u);
     src[dst] = (uint32_t)i;
 }
@@ -250,8 +271,10 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     const Geo& geo = BATCH ? rp->geo : geo_p;
     const Phys& ph_g = BATCH ? rp->ph : ph_p;
     const uint32_t i = src[a];
+    if (i >= (uint32_t)cap) return;        // slot never written (counts inconsistent: reported)
     const uint32_t cg = cellof[i];
     const uint32_t b = start[cg], e = start[cg + 1];
+    if (e > (uint32_t)cap || b > e) return;
     const uint32_t kk = key[a];
     uint32_t r = 0, nm = 0;
     for (uint32_t q = b; q < e; ++q) {
@@ -383,26 +406,29 @@ __global__ void k_scatter_type_by_id(int n, const uint32_t* __restrict__ id,
 
 void launch_bin_count(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                       const MaskDev& mk, const Master& m, bool kick, uint32_t* cellof,
-                      uint32_t* slot, uint32_t* count, uint32_t* status)
+                      uint32_t* slot, uint32_t* count, uint32_t* tsum, uint32_t* status)
 {
     if (n <= 0) return;
     launch_pdl(kick ? k_bin_count<false, true> : k_bin_count<false, false>, dim3(nblocks(n)),
-               dim3(BLOCK), st, n, cap, geo, ph, Batch{}, mk, m, cellof, slot, count, status);
+               dim3(BLOCK), st, n, cap, geo, ph, Batch{}, mk, m, cellof, slot, count, tsum,
+               status);
 }
 
 void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
                             bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
-                            uint32_t* status)
+                            uint32_t* tsum, uint32_t* status)
 {
     if (bt.nchunk <= 0) return;
     launch_pdl_smem(kick ? k_bin_count<true, true> : k_bin_count<true, false>, dim3(bt.nchunk),
                     dim3(BATCH_CHUNK), REP_SMEM, st, 0, cap, Geo{}, Phys{}, bt, MaskDev{}, m,
-                    cellof, slot, count, status);
+                    cellof, slot, count, tsum, status);
 }
 
 int scan_num_blocks(int64_t n) { return (int)((n + SCAN_TILE - 1) / SCAN_TILE); }
 
-int scan_num_launches(int64_t) { return 2; }
+int scan_num_launches(int64_t n) { return scan_fused_sums(n) ? 1 : 2; }
+
+bool scan_fused_sums(int64_t n) { return scan_num_blocks(n) <= 64; }
 
 void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
                            bool zero_in)
@@ -410,14 +436,25 @@ void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* o
     const int nb = scan_num_blocks(n);
     if (nb <= 0) return;
     launch_pdl(k_scan_blocks, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp);
-    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp, nb, out, (int)zero_in);
+    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, tmp, nb, out, (int)zero_in,
+               (uint32_t*)nullptr);
+}
+
+void launch_scan_from_sums(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out,
+                           const uint32_t* sums, uint32_t* zero_sums)
+{
+    const int nb = scan_num_blocks(n);
+    if (nb <= 0) return;
+    launch_pdl(k_scan_apply, dim3(nb), dim3(SCAN_THREADS), st, in, n, sums, nb, out, 1, zero_sums);
 }
 
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
-                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src)
+                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src,
+                        uint32_t* status)
 {
     if (n <= 0) return;
-    launch_pdl(k_bin_scatter, dim3(nblocks(n)), dim3(BLOCK), st, n, cellof, slot, start, id, key, src);
+    launch_pdl(k_bin_scatter, dim3(nblocks(n)), dim3(BLOCK), st, n, cellof, slot, start, id, key, src,
+               status);
 }
 
 void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,

@@ -245,16 +245,26 @@ constexpr int OBS_PARTIALS = 16;   // observable slots per partial (14 used)
 // ---- launchers (binning / scan) -------------------------------------------
 // Cell of every particle from the master positions m.x, and its arrival rank
 // in the cell (atomic order); kick: first the step's first half-kick, drift
-// and reflection.
+// and reflection.  tsum (scan_num_blocks(ncell) words, zero on entry) receives
+// the scan's per-tile sums of the counts.
 void launch_bin_count(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                       const MaskDev& mk, const Master& m, bool kick, uint32_t* cellof,
-                      uint32_t* slot, uint32_t* count, uint32_t* status);
+                      uint32_t* slot, uint32_t* count, uint32_t* tsum, uint32_t* status);
 int scan_num_blocks(int64_t n);
+// Whether the binning of a lattice of n cells forms the scan's tile sums in
+// its count kernel (few tiles) or in a launch of their own.
+bool scan_fused_sums(int64_t n);
+// Launches of the binning's scan.
 int scan_num_launches(int64_t n);
 // Exclusive scan of in[0..n) into out[0..n]; tmp holds scan_num_blocks(n) + 1
 // words; zero_in clears in[] after it is read.
 void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
                            bool zero_in = false);
+// The same in one launch, given the tile sums (from launch_bin_count); the
+// counts are cleared as they are read, and so is zero_sums (the other tile-sum
+// buffer, for the next binning).
+void launch_scan_from_sums(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out,
+                           const uint32_t* sums, uint32_t* zero_sums);
 // For every scattered slot a: the particle's place s in its cell (rank of
 // key[a] = frozen << 31 | id among the cell's keys), and the gather of master
 // state in[src[a]] to out[s] with the cell-ordered compute arrays (pos4, vel4,
@@ -270,7 +280,8 @@ void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
                               void* pos4, void* vel4, uint32_t* cell_s, uint32_t* mend);
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
-                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src);
+                        const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src,
+                        uint32_t* status);
 // Sorts each cell's slots by key and clears count[] for the next binning.
 void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uint32_t* key,
                       uint32_t* src, uint32_t* count);
@@ -326,7 +337,7 @@ void launch_load_state_batch(cudaStream_t st, int64_t cap, const double* pos3, c
                              const uint8_t* type_by_id, uint32_t* status);
 void launch_bin_count_batch(cudaStream_t st, int64_t cap, const Batch& bt, const Master& m,
                             bool kick, uint32_t* cellof, uint32_t* slot, uint32_t* count,
-                            uint32_t* status);
+                            uint32_t* tsum, uint32_t* status);
 // shape: code shape of the thread-per-particle kernel (0 or 1; same results).
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,
                              const void* pos4, const uint32_t* cell_s, const uint32_t* start,
