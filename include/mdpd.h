@@ -167,8 +167,11 @@ int mdpd_num_particles(const mdpd_handle* h, int64_t* n);
 int mdpd_step_count(const mdpd_handle* h, int64_t* steps);
 
 /* Copy the state to host arrays in id order: pos/vel 3N doubles, type N,
- * rho N (the local density of the last force evaluation).  Any pointer may
- * be NULL.  Synchronises. */
+ * rho N (the local density of the last force evaluation).  This is the state
+ * of Algorithm 1 after its last line: x(t + dt), v(t + dt) and the density
+ * rho_i of Sec. 2.1 at x(t + dt).  Any pointer may be NULL.  Errors:
+ * INVALID_ARG (NULL handle), NONFINITE / OUT_OF_BOX raised by the last steps,
+ * CUDA.  Synchronises. */
 int mdpd_get_state(mdpd_handle* h, double* pos, double* vel, int32_t* type,
                    double* rho);
 
@@ -200,15 +203,21 @@ int mdpd_set_state_accel(mdpd_handle* h, const double* pos, const double* vel,
                          const double* accel);
 
 /* Evaluate, without stepping, the density and the forces at the current
- * positions and velocities with the current step index: force gets 3N doubles
+ * positions and velocities with the current step index: the local density
+ * rho_i of Sec. 2.1 and the pair forces F^C + F^D + F^R of Sec. 2.1 and Eq. 1
+ * (Algorithm 1 lines 4 and 6 without the integration).  force gets 3N doubles
  * (sum_j F_ij + g for mobile particles, m = 1; 0 for frozen ones), rho N
- * doubles, id order.  Either pointer may be NULL.  Synchronises. */
+ * doubles, id order.  Either pointer may be NULL.  Errors: INVALID_ARG,
+ * NONFINITE, CUDA.  Synchronises. */
 int mdpd_forces(mdpd_handle* h, double* force, double* rho);
 
 /* Device-array variant of mdpd_forces. */
 int mdpd_forces_dev(mdpd_handle* h, double* force, double* rho);
 
-/* Observables of the last force evaluation, reduced in FP64 in a fixed order:
+/* Observables of the last force evaluation (the pressure-tensor and
+ * temperature checks of Sec. 4.1: the surface tension there is built from
+ * the diagonal of the pressure tensor, kinetic part plus the virial below),
+ * reduced in FP64 in a fixed order:
  * out[0..2] momentum, out[3] kinetic energy, out[4] kT = 2 KE / (3 (N_m - 1)),
  * out[5..10] conservative virial 1/2 sum_{i mobile} sum_j r_ij,a F^C_ij,b
  * (xx yy zz xy xz yz), out[11..13] sum v_a^2, out[14] N_m (mobile count),
@@ -342,15 +351,23 @@ int mdpd_describe(const mdpd_handle* h, int32_t ncell[3], int32_t* launches_per_
  * __device__ array of the library (about 4.3 MB, held by every GPU that
  * loads the library until the process exits); it calls no allocator.
  * params: box, periodic, rc, rd, precision and rho_self are used.
- * pos: device array of 3n doubles (interleaved xyz, inside the box on
- * non-periodic axes); rho: device array of n doubles, written in input order.
+ * pos: device array of 3n doubles (interleaved xyz); on non-periodic axes
+ * positions must lie in [lo, lo + L] (the upper face included).  A particle
+ * outside that range, or with a non-finite coordinate, gets rho = NaN, and
+ * the densities of its neighbours are then undefined too.
+ * rho: device array of n doubles, written in input order.
  * Limits: n <= 65536 and at most 32768 cells of edge >= rc; larger inputs
  * fail with MDPD_ERR_INVALID_ARG (message from mdpd_last_error(NULL)).
- * Asynchronous on cuda_stream (NULL = legacy default stream).  The first call
- * on each device looks up the array's device address; make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and give wrong
- * results. */
+ * Errors: INVALID_ARG (the limits, NULL arrays, rd > rc, bad box),
+ * CUDA (a CUDA error already pending before the call is reported, not
+ * cleared; a failed launch is named in the message).
+ * Asynchronous on cuda_stream (NULL = legacy default stream).  Outside
+ * stream capture every call looks up the array's device address afresh, so
+ * cudaDeviceReset between calls is harmless; a call made while cuda_stream is
+ * being captured reuses the address found by the last uncaptured call on the
+ * device, so make the first call on a device before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give wrong results. */
 int mdpd_density_noalloc(const mdpd_params* params, int64_t n, const double* pos,
                          double* rho, void* cuda_stream);
 
@@ -362,6 +379,10 @@ int mdpd_density_noalloc(const mdpd_params* params, int64_t n, const double* pos
  * NULL) the best launch time.  Errors: INVALID_ARG (NULL output), CUDA. */
 int mdpd_measure_fma_peak(double* lane_ops_per_s, double* best_ms);
 
+/* Release a handle: waits for its stream, frees every device buffer and
+ * captured graph it owns and, if it created its stream, that stream (the end
+ * of the run of Algorithm 1; the paper's code leaves this to its host
+ * framework).  NULL is accepted and ignored.  No error is reported. */
 void mdpd_destroy(mdpd_handle* h);
 
 /* Message of the last error on h (or of the last failed mdpd_create when h is

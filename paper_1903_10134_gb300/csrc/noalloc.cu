@@ -11,13 +11,17 @@
 // exits.
 //
 // Host code may not use the array's name as a device address (in host code it
-// names a host-side stand-in).  The device address is looked up once per device
-// with cudaGetSymbolAddress, with that device current, the first time the entry
-// point runs on it; that first call should therefore happen before any stream
-// capture.  All calls share the array and it keeps the previous call's contents,
+// names a host-side stand-in).  The device address is looked up with
+// cudaGetSymbolAddress, with the device current, on every call made outside
+// stream capture (so a cudaDeviceReset between calls leaves no stale address);
+// a call made while its stream is being captured reuses the address of the
+// last uncaptured call on that device, so the first call on a device should
+// happen before any stream capture.  All calls share the array and it keeps the previous call's contents,
 // so the counters that must start at zero are cleared on every call, and calls
 // whose work overlaps on the GPU (on different streams, or from several host
 // threads without ordering) race on the array and give wrong results.
+#include <math_constants.h>
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -59,8 +63,13 @@ constexpr int NA_MAX_DEVICES = 64;
 std::mutex g_na_mutex;
 void* g_na_ptr[NA_MAX_DEVICES] = {};
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_address(void** out, std::string& why)
+// Device address of the scratch array on the current device.  Outside stream
+// capture it is looked up on every call (a lookup allocates nothing), so a
+// cudaDeviceReset or a new primary context between calls cannot leave a
+// stale address behind; while the stream is being captured the address
+// recorded by the last uncaptured call on this device is used, and a call
+// that has none is refused.
+int scratch_address(cudaStream_t st, void** out, std::string& why)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -72,8 +81,14 @@ int scratch_address(void** out, std::string& why)
         why = "device index out of range for the scratch table";
         return MDPD_ERR_INVALID_ARG;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) {
+        why = std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e);
+        return MDPD_ERR_CUDA;
+    }
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess || !p) {
@@ -81,9 +96,26 @@ int scratch_address(void** out, std::string& why)
             return MDPD_ERR_CUDA;
         }
         g_na_ptr[dev] = p;
+    } else if (!g_na_ptr[dev]) {
+        why = "the first call on a device must come before any stream capture";
+        return MDPD_ERR_INVALID_ARG;
     }
     *out = g_na_ptr[dev];
     return MDPD_OK;
+}
+
+// Whether position x lies outside the box on a non-periodic axis (the closed
+// upper face is accepted: a particle on it is binned into the last cell, where
+// the search of the neighbouring cells stays complete), or is not finite.
+__device__ __forceinline__ bool na_outside(const double* __restrict__ x, const Geo& geo)
+{
+    bool out = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (!isfinite(x[k])) out = true;
+        else if (!geo.periodic[k] && (x[k] < geo.lo[k] || x[k] > geo.hi[k])) out = true;
+    }
+    return out;
 }
 
 __global__ void k_na_count(int n, const double* __restrict__ pos, Geo geo,
@@ -139,13 +171,18 @@ __global__ void k_na_gather(int n, const double* __restrict__ pos, const uint32_
     cell_s[s] = c;
 }
 
+// Densities back to input order; a particle outside the box on a
+// non-periodic axis (or with a non-finite coordinate) gets NaN, so a bad
+// input shows in the output instead of as a silently clamped cell.
 template <typename T>
-__global__ void k_na_unsort(int n, const uint32_t* __restrict__ src, const T* __restrict__ r,
+__global__ void k_na_unsort(int n, const double* __restrict__ pos, Geo geo,
+                            const uint32_t* __restrict__ src, const T* __restrict__ r,
                             double* __restrict__ out)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n) return;
-    out[src[s]] = (double)r[s];
+    const uint32_t i = src[s];
+    out[i] = na_outside(pos + 3 * (int64_t)i, geo) ? CUDART_NAN : (double)r[s];
 }
 
 }  // namespace
@@ -158,7 +195,7 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
                                     double* rho, void* cuda_stream)
 {
     std::string why;
-    auto bad = [&](int code, const std::string& msg) {
+    auto bad = [&](int code, const std::string& msg) -> int {
         set_global_error("mdpd_density_noalloc: " + msg);
         return code;
     };
@@ -198,8 +235,15 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
     ph.rd = p->rd;
     ph.rho_self = p->rho_self ? 1 : 0;
     fill_derived(ph, geo);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // an error left by earlier, unrelated work is not this call's: report it
+    // without clearing it
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess)
+        return bad(MDPD_ERR_CUDA, std::string("a CUDA error was pending before the call: ") +
+                                      cudaGetErrorString(e));
     void* base = nullptr;
-    int rc = scratch_address(&base, why);
+    int rc = scratch_address(st, &base, why);
     if (rc) return bad(rc, why);
     if (n == 0) return MDPD_OK;
 
@@ -214,25 +258,36 @@ extern "C" int mdpd_density_noalloc(const mdpd_params* p, int64_t n, const doubl
     uint32_t* cells = (uint32_t*)(b + OFF_CELLS);
     void* pos4 = b + OFF_POS4;
     void* rs = b + OFF_RHO;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     const int nn = (int)n;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    cudaError_t e = cudaMemsetAsync(count, 0, (size_t)geo.ncell * sizeof(uint32_t), st);
+    // the first failing step names itself (launch errors are this call's own,
+    // so they are cleared after being read)
+    auto check = [&](const char* what) -> int {
+        const cudaError_t le = cudaPeekAtLastError();
+        if (le == cudaSuccess) return MDPD_OK;
+        cudaGetLastError();
+        return bad(MDPD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(le));
+    };
+    e = cudaMemsetAsync(count, 0, (size_t)geo.ncell * sizeof(uint32_t), st);
     if (e != cudaSuccess) return bad(MDPD_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
     k_na_count<<<nb, 256, 0, st>>>(nn, pos, geo, cellof, slot, count);
+    if ((rc = check("k_na_count"))) return rc;
     launch_exclusive_scan(st, count, geo.ncell, start, scan);
+    if ((rc = check("cell-count scan"))) return rc;
     k_na_scatter<<<nb, 256, 0, st>>>(nn, cellof, slot, start, key, src);
+    if ((rc = check("k_na_scatter"))) return rc;
     launch_cell_sort(st, geo.ncell, start, key, src, count);
+    if ((rc = check("cell sort"))) return rc;
     if (p->precision == 0)
         k_na_gather<double><<<nb, 256, 0, st>>>(nn, pos, src, cellof, geo, (D4*)pos4, cells);
     else
         k_na_gather<float><<<nb, 256, 0, st>>>(nn, pos, src, cellof, geo, (float4*)pos4, cells);
+    if ((rc = check("k_na_gather"))) return rc;
     launch_density(st, p->precision, nn, geo, ph, pos4, cells, start, rs);
+    if ((rc = check("density pass"))) return rc;
     if (p->precision == 0)
-        k_na_unsort<double><<<nb, 256, 0, st>>>(nn, src, (const double*)rs, rho);
+        k_na_unsort<double><<<nb, 256, 0, st>>>(nn, pos, geo, src, (const double*)rs, rho);
     else
-        k_na_unsort<float><<<nb, 256, 0, st>>>(nn, src, (const float*)rs, rho);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return bad(MDPD_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
-    return MDPD_OK;
+        k_na_unsort<float><<<nb, 256, 0, st>>>(nn, pos, geo, src, (const float*)rs, rho);
+    return check("k_na_unsort");
 }

@@ -290,3 +290,59 @@ def test_oracle_results_do_not_depend_on_thread_count():
     O.set_num_threads(n0)
     for u, v in zip(*out):
         assert np.array_equal(u, v)
+
+
+# --- the subset force routine used as the checker at full size ----------------------
+
+def _walled_rock_standin(seed):
+    """A small walled porous system shaped like the rock workload: a Gaussian
+    random field thresholded to pores, fluid at density 6 in the pores and
+    frozen wall particles (type 1) in a 1 r_c shell, body force along x."""
+    rng = np.random.default_rng(seed)
+    nvox, voxel = 16, 0.5
+    f = I.gaussian_random_field(nvox, 2.0, rng)
+    mask = (f >= np.quantile(f, 0.35)).astype(np.uint8)
+    L = nvox * voxel
+    p = I.MDPDParams(box=(L, L, L), ntypes=2, g=(0.05, 0.0, 0.0), frozen_types=(1,))
+    p.set_pair(0, 1, A=-30.0)
+    pore = np.argwhere(mask == 0)                       # [z, y, x]
+    pick = pore[rng.integers(0, len(pore), size=int(6.0 * len(pore) * voxel ** 3))]
+    fluid = (pick[:, ::-1] + rng.random(pick.shape)) * voxel
+    walls, _ = O.place_walls(mask, (1, 1, 1), voxel, (0.0, 0.0, 0.0), 6.0, 1.0, seed + 7)
+    pos = np.concatenate([fluid, walls])
+    vel = np.concatenate([I.maxwell_velocities(len(fluid), 1.0, rng), np.zeros_like(walls)])
+    typ = np.concatenate([np.zeros(len(fluid), np.int32), np.ones(len(walls), np.int32)])
+    return p, pos, vel, typ, mask, voxel
+
+
+def _subset_cases():
+    w = I.tiny(600, (5.0, 5.0, 5.0), 31, ntypes=3)
+    yield "multi-type, frozen, body force", w.params.copy(
+        frozen_types=(2,), g=(0.02, -0.01, 0.005)), w.pos, w.vel, w.type, {}
+    w = I.tiny(500, (4.0, 3.0, 5.0), 32, periodic=(1, 0, 1), ntypes=2)
+    yield "reflecting axis, Gaussian xi", w.params.copy(xi_dist=1, g=(0.0, 0.0, 0.03)), \
+        w.pos, w.vel, w.type, {}
+    p, pos, vel, typ, mask, voxel = _walled_rock_standin(33)
+    yield "walled rock stand-in", p, pos, vel, typ, {"mask": mask, "voxel": voxel}
+
+
+@pytest.mark.parametrize("use_cells", [False, True])
+def test_forces_subset_equals_full_forces_bitwise(use_cells):
+    """orc_forces_subset, the checker of every full-size sampled parity test,
+    is a second loop over the same candidates; on every sampled particle it
+    must give exactly the accelerations of orc_forces (Sec. 2.1, Eq. 1), with
+    the same summation order, so the two may not differ in a single bit."""
+    rng = np.random.default_rng(34)
+    for name, p, pos, vel, typ, walls in _subset_cases():
+        o = O.Oracle(p, pos, vel, typ, 5, use_cells=use_cells, **walls)
+        o.step = 17
+        rho = o.density()
+        a, _ = o.forces(rho=rho, step=17)
+        idx = np.concatenate([rng.choice(o.n, size=min(150, o.n), replace=False),
+                              [0, o.n - 1]])
+        sub = o.forces_subset(idx, rho=rho, step=17)
+        assert np.array_equal(sub, a[idx]), name
+        # frozen rows are zero, mobile rows carry the body force
+        frozen = np.isin(typ[idx], np.array(p.frozen_types, dtype=np.int32))
+        assert np.all(sub[frozen] == 0.0), name
+        assert np.any(sub[~frozen] != 0.0), name
