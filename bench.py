@@ -271,12 +271,13 @@ OBS_NAMES = ("px", "py", "pz", "ke", "kT", "Wxx", "Wyy", "Wzz", "Wxy", "Wxz", "W
              "sum_vx2", "sum_vy2", "sum_vz2")
 
 
-def fp64_leg(mdpd, args, stream, pairs32):
+def fp64_leg(mdpd, args, stream, workload=None):
     """The same workload with FP64 pair arithmetic: autotuned, warmed up, then
     min(K, 100) steps timed with CUDA events (same L2 rule as the FP32 run)."""
     import torch
-    w = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
-    if args.workload == "batch":
+    workload = workload or args.workload
+    w = make_workload(workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
+    if workload == "batch":
         s = mdpd.Batch.from_workloads(w, stream=stream)
     else:
         s = mdpd.System.from_workload(w, stream=stream)
@@ -362,6 +363,53 @@ def precision_error(mdpd, s, w, workload):
             "note": "per particle |f32 - f64| / max(|f64|, rms f64) and |rho32 - rho64| / "
                     "max(rho64, mean rho64); momentum relative to sum |v|; one force evaluation "
                     "at the final state"}
+
+
+def oracle_error(mdpd, s, w, workload):
+    """Error of the FP32 path against the FP64 oracle (spec change 1) on
+    the bench's final state: the GPU evaluates densities, forces and
+    observables once at its current state and step index (mdpd_forces), and
+    the oracle evaluates the same state (positions, velocities, types, wall
+    particles included, same seed and step) in FP64 on the host cores.  Every
+    particle is compared; for a batch, replica 0."""
+    import numpy as np
+    from oracle import oracle as O
+    x, v, t, _ = s.state()
+    step = mdpd.mdpd_step_count(s.h)
+    f32, rho32 = s.forces()
+    if workload == "batch":
+        w0 = w[0]
+        a, b = 0, w0.n
+        x, v, t, f32, rho32 = x[a:b], v[a:b], t[a:b], f32[a:b], rho32[a:b]
+        obs32 = s.observables()[0]
+        p, seed = w0.params, w0.seed
+    else:
+        obs32 = s.observables()
+        p, seed = w.params, w.seed
+    t0 = time.perf_counter()
+    o = O.Oracle(p.copy(precision=0), x, v, t, seed, use_cells=True, step=step)
+    el = time.perf_counter() - t0
+    f64, rho64 = o.a, o.rho
+    obs64 = o.observables()
+    mob = ~np.isin(t, np.array(p.frozen_types, dtype=np.int32))
+    fn = np.linalg.norm(f64[mob], axis=1)
+    rms = float(np.sqrt(np.mean(fn ** 2))) if fn.size else 1.0
+    ferr = np.linalg.norm(f32[mob] - f64[mob], axis=1) / np.maximum(fn, rms)
+    rerr = np.abs(rho32 - rho64) / np.maximum(np.abs(rho64), max(float(np.mean(rho64)), 1e-30))
+    scale = {k: abs(obs64[k]) for k in range(14)}
+    for k in range(3):
+        scale[k] = float(np.abs(v[mob, k]).sum())
+    obs_err = {OBS_NAMES[k]: float(abs(obs32[k] - obs64[k]) / max(scale[k], 1e-30))
+               for k in range(14)}
+    return {"vs": "FP64 CPU oracle (oracle/), same state, step index and seed",
+            "n": int(len(x)), "mobile": int(mob.sum()), "oracle_seconds": el,
+            "force_rel_max": float(ferr.max()) if ferr.size else 0.0,
+            "force_rel_rms": float(np.sqrt(np.mean(ferr ** 2))) if ferr.size else 0.0,
+            "density_rel_max": float(rerr.max()), "observables_rel": obs_err,
+            "tolerance": {"force": 1e-5, "density": 2e-6},
+            "note": "per mobile particle |f32 - f64| / max(|f64|, rms f64); every particle's "
+                    "|rho32 - rho64| / max(rho64, mean rho64); momentum relative to sum |v|; "
+                    "the virial from the oracle's full force evaluation"}
 
 
 def dist_setup():
@@ -452,6 +500,55 @@ def aggregate_ranks(ms: float, n: int, steps: int, world: int, device=None):
 def replica_seed(rank: int) -> int:
     """Seed of the replica advanced by a rank (independent replicas)."""
     return 1 + rank
+
+
+def slab_leg(mdpd, args, stream):
+    """The liquid-vapour slab (N = 48,000) beside the headline: FP32
+    throughput (L2 flushed between timed steps), the same with FP64 pair
+    arithmetic, and the FP32 error against both the FP64 GPU path and the FP64
+    oracle on the final state."""
+    import torch
+    w = make_workload("slab", 1, seed=1)
+    s = mdpd.System.from_workload(w, stream=stream)
+    try:
+        res = s.autotune()
+        for _ in range(5):
+            s.step(1)
+        s.sync()
+        K = max(3, min(args.steps, 200))
+        flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32,
+                                device=torch.cuda.current_device())
+        ms = 0.0
+        for _ in range(K):
+            with torch.cuda.stream(stream):
+                flush_buf.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(1)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms += a.elapsed_time(b)
+        s.sync()
+        pairs = s.pair_count()
+        value = s.n * K / (ms * 1e-3)
+        out = {"workload": "slab", "desc": DESC["slab"], "n": s.n, "steps": K,
+               "value": value, "unit": "particle-steps/s", "ms_per_step": ms / K,
+               "pair_evals_per_s": value * pairs / 2 / s.n, "dtype": "f32",
+               "autotune": {"density": {mdpd.KERNELS_NLIST: "nlist",
+                                        mdpd.KERNELS_NLIST_THREAD: "nlist-thread"}[res[0]],
+                            "force_lanes": res.lanes},
+               "l2": "flushed between timed steps"}
+        if not args.no_error:
+            out["fp32_error"] = precision_error(mdpd, s, w, "slab")
+        if not args.no_oracle_error:
+            out["oracle_error"] = oracle_error(mdpd, s, w, "slab")
+    finally:
+        s.close()
+    if not args.no_fp64:
+        out["fp64"] = fp64_leg(mdpd, args, stream, workload="slab")
+        out["fp32_speedup_vs_fp64"] = out["value"] / out["fp64"]["value"]
+    return out
 
 
 def run_ours(args):
@@ -559,32 +656,42 @@ def run_ours(args):
             cand += candidate_tests(xs[off:off + nr], p, ncell, fz)
             off += nr
 
-    # end-to-end through the host-pointer C ABI: per step upload x, v from
-    # pinned host memory, one step, read x, v back into pinned host memory
+    # end-to-end through the host-pointer C ABI: every step uploads the state
+    # a caller resumes from (x, v and the accelerations of the next
+    # half-kick) from pinned host memory with mdpd_set_state_accel (which
+    # evaluates no forces), advances one step, and reads the same three arrays
+    # back into pinned host memory
     e2e = None
     if not args.no_e2e:
         x, v, _, _ = s.state()
+        acc = mdpd.mdpd_get_accel(s.h)
         hx = torch.from_numpy(x).pin_memory().numpy()
         hv = torch.from_numpy(v).pin_memory().numpy()
-        ke = max(3, min(K, 200))
-        for _ in range(2):
-            mdpd.mdpd_set_state(s.h, hx, hv)
+        ha = torch.from_numpy(acc).pin_memory().numpy()
+        ke = max(3, min(K, 50 if n > 10 ** 6 else 200))
+
+        def e2e_step():
+            mdpd.mdpd_set_state_accel(s.h, hx, hv, ha)
             s.step(1)
             mdpd.mdpd_get_state(s.h, hx, hv, want_type=False, want_rho=False)
+            mdpd.mdpd_get_accel(s.h, ha)
+
+        for _ in range(2):
+            e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(ke):
-            mdpd.mdpd_set_state(s.h, hx, hv)
-            s.step(1)
-            mdpd.mdpd_get_state(s.h, hx, hv, want_type=False, want_rho=False)
+            e2e_step()
         el = time.perf_counter() - t0
         et = torch.tensor([el], dtype=torch.float64, device=dev)
         if world > 1:
             torch.distributed.all_reduce(et, op=torch.distributed.ReduceOp.MAX)
         e2e = {"value": world * n * ke / float(et.item()), "unit": "particle-steps/s",
-               "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes),
-               "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes),
-               "steps": ke, "api": "mdpd_set_state + mdpd_step(1) + mdpd_get_state"}
+               "h2d_bytes_per_step": int(hx.nbytes + hv.nbytes + ha.nbytes),
+               "d2h_bytes_per_step": int(hx.nbytes + hv.nbytes + ha.nbytes),
+               "steps": ke,
+               "api": "mdpd_set_state_accel + mdpd_step(1) + mdpd_get_state + mdpd_get_accel "
+                      "(host buffers; no force evaluation besides the step's own)"}
 
     if rank == 0:
         peaks = measured_peaks()
@@ -627,10 +734,15 @@ def run_ours(args):
         dom = max((k for k in kern if kern[k]), key=lambda k: kern[k]["ms"], default=None)
         fp64 = None
         if prec == 1 and not args.no_fp64:
-            fp64 = fp64_leg(mdpd, args, stream, pairs)
-        err = None
+            fp64 = fp64_leg(mdpd, args, stream)
+        err = orc_err = None
         if prec == 1 and not args.no_error:
             err = precision_error(mdpd, s, w, args.workload)
+        if not args.no_oracle_error:
+            orc_err = oracle_error(mdpd, s, w, args.workload)
+        slab = None
+        if args.workload != "slab" and not args.no_slab and world == 1:
+            slab = slab_leg(mdpd, args, stream)
         cpu = None
         if not args.no_cpu_baseline and world == 1:
             wc = make_workload(args.workload, 0, seed=1, nvox=args.nvox, nrep=args.nrep)
@@ -690,7 +802,9 @@ def run_ours(args):
             "gpu_launches": launches,
             "cpu_baseline": cpu,
             "fp32_error": err,
+            "oracle_error": orc_err,
             "fp64": fp64,
+            "slab": slab,
             "e2e": e2e,
             "clocks": clk,
         }
@@ -706,7 +820,7 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=tuple(DESC), default="slab")
+    ap.add_argument("--workload", choices=tuple(DESC), default="rock")
     ap.add_argument("--precision", choices=("fp32", "fp64"), default="fp32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true",
@@ -716,6 +830,10 @@ def main():
                     help="skip the FP64 throughput leg after the FP32 run")
     ap.add_argument("--no-error", action="store_true",
                     help="skip the FP32-vs-FP64 error evaluation after the timed steps")
+    ap.add_argument("--no-oracle-error", action="store_true",
+                    help="skip the FP32-vs-oracle error evaluation after the timed steps")
+    ap.add_argument("--no-slab", action="store_true",
+                    help="skip the slab leg (FP32 vs FP64) beside a non-slab headline")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=60.0)
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")

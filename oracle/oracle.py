@@ -177,11 +177,12 @@ class Oracle:
 
     State (pos, vel, acc, rho) is kept in input order with ids 0..n-1.  On
     construction the density and the forces of the initial state are
-    evaluated with step index 0, as the library does at creation.
+    evaluated with step index `step` (0 by default, as the library does at
+    creation).
     """
 
     def __init__(self, params, pos, vel, type, seed: int, mask=None, voxel=0.0,
-                 origin=(0.0, 0.0, 0.0), use_cells=None, ids=None):
+                 origin=(0.0, 0.0, 0.0), use_cells=None, ids=None, step: int = 0):
         self.params = params
         self.x = _c(pos, np.float64).copy()
         self.v = _c(vel, np.float64).copy()
@@ -194,7 +195,7 @@ class Oracle:
         self.sys, self._mask = make_sys(params, seed, use_cells, mask, voxel, origin)
         self.a = np.zeros_like(self.x)
         self.rho = np.zeros(n)
-        self.step = 0
+        self.step = int(step)
         self.virial = np.zeros(6)
         self.refresh()
 

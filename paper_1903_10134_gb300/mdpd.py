@@ -363,8 +363,12 @@ def mdpd_describe(h):
     return nc.tolist(), int(lps.value)
 
 
-def mdpd_get_accel(h) -> np.ndarray:
-    a = np.zeros((mdpd_num_particles(h), 3))
+def mdpd_get_accel(h, out=None) -> np.ndarray:
+    """Accelerations the next half-kick uses (n, 3), into `out` if given (a
+    C-contiguous float64 buffer, e.g. pinned host memory viewed as numpy)."""
+    n = mdpd_num_particles(h)
+    a = np.zeros((n, 3)) if out is None else out
+    assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == 3 * n
     _check(lib().mdpd_get_accel(h, _p(a)), h)
     return a
 
