@@ -107,8 +107,9 @@ int mdpd_create_dev(const mdpd_params* params, int64_t n, const double* pos,
  * replica the random stream is keyed on the particle's index inside the
  * replica, so replica r evolves bit-identically to mdpd_create() of
  * (params[r], n[r] particles, seeds[r]) run alone with the same kernel
- * variant.  Walls, the force VJP and the wall density are not available on a
- * batch handle.  mdpd_step, mdpd_get_state/set_state(_dev), mdpd_forces(_dev),
+ * variant.  Walls and the wall density are not available on a batch handle;
+ * the VJPs and windows are, with per-replica parameter gradients.
+ * mdpd_step, mdpd_get_state/set_state(_dev), mdpd_forces(_dev),
  * mdpd_set_step, mdpd_sync, mdpd_pair_count (summed over replicas),
  * mdpd_profile, mdpd_set_option and mdpd_autotune apply to the whole batch;
  * the observables are per replica (mdpd_batch_observables).
@@ -302,29 +303,74 @@ int mdpd_set_step(mdpd_handle* h, int64_t step);
  * will use: a(t) of the current state.  Synchronises. */
 int mdpd_get_accel_dev(mdpd_handle* h, double* accel);
 
-/* Vector-Jacobian product of one force evaluation (the adjoint of Sec. 2.1 /
- * Eq. 1 at a fixed random stream), at the current positions, the current
- * velocities (those the dissipative term sees) and the current step index.
- * abar: device, 3N doubles (id order), the adjoint of the accelerations
- * a_i = sum_j F_ij + g of mobile particles (rows of frozen particles are
- * ignored).  Outputs (device, may be NULL): xbar, ubar 3N doubles (id order):
- * d(sum_i abar_i . a_i)/dx and /du, the position part including the path
- * through the local densities rho_i; theta_bar 3*8*8 doubles: the gradient with
- * respect to the symmetric tables A, B, gamma ([q][a][b] = [q][b][a] = dL/dP_ab;
- * the gamma entry includes sigma = sqrt(2 gamma kT)).  Parameter gradients are
- * summed with floating-point atomics (last-bit differences between runs).
- * Errors: TILE_OVERFLOW if a particle has more than 64 partners within r_c.
+/* Vector-Jacobian product of one evaluation of Sec. 2.1 / Eq. 1 (the local
+ * densities rho_i, the accelerations a_i = sum_j F_ij + g of mobile
+ * particles and the conservative virial W of mdpd_observables, whose
+ * diagonal builds the pressure tensor and surface tension of Sec. 4.1) at
+ * the current positions, the current velocities (those the dissipative term
+ * sees) and the current step index, with the random draws of that step held
+ * fixed:  L = sum_i abar_i . a_i + sum_r sum_k cvir[6r + k] W_k(replica r)
+ *            + sum_i rhobar_i rho_i.
+ * Inputs (device, each may be NULL = zero): abar 3N doubles (id order; rows
+ * of frozen particles are ignored), cvir 6 doubles per replica (xx yy zz xy
+ * xz yz weights, the order of mdpd_observables), rhobar N doubles.
+ * Outputs (device, may be NULL): xbar, ubar 3N doubles (id order): dL/dx
+ * (including the path through the local densities) and dL/du; theta_bar
+ * 3*8*8 doubles per replica (replica-major): the gradient with respect to
+ * the symmetric tables A, B, gamma ([q][a][b] = [q][b][a] = dL/dP_ab; the
+ * gamma entry includes sigma = sqrt(2 gamma kT)).  The parameter gradients
+ * are reduced in a fixed order, so repeated calls agree bit for bit.  The
+ * state is not changed.  Errors: INVALID_ARG (a host pointer),
+ * TILE_OVERFLOW (a particle with more than 64 partners within r_c), CUDA.
  * Synchronises. */
+int mdpd_eval_vjp_dev(mdpd_handle* h, const double* abar, const double* cvir,
+                      const double* rhobar, double* xbar, double* ubar, double* theta_bar);
+
+/* mdpd_eval_vjp_dev with abar only (the force VJP of Sec. 2.1 / Eq. 1);
+ * abar is required. */
 int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
                        double* theta_bar);
 
-/* Vector-Jacobian product of the density pass alone (Sec. 2.1): xbar (device,
- * N x 3, id order) = d(sum_i rhobar_i rho_i)/dx at the current positions, for
- * rhobar (device, N doubles, id order); every particle's density counts,
- * frozen ones included.  Used to differentiate a loss on the local densities.
- * Not on a batch handle.  Errors: INVALID_ARG, TILE_OVERFLOW (more than 64
- * partners within r_c), CUDA.  Synchronises. */
+/* mdpd_eval_vjp_dev with rhobar only: xbar (device, 3N, id order) =
+ * d(sum_i rhobar_i rho_i)/dx of the local densities of Sec. 2.1; every
+ * particle's density counts, frozen ones included.  Both pointers are
+ * required. */
 int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar);
+
+/* Record a velocity-Verlet window for its adjoint: advance nsteps steps of
+ * Algorithm 1 (as mdpd_step) from the current state and step index s0,
+ * keeping every step's positions x_k and half-step velocities
+ * v'_k = v_k + (dt/2) a_k in device memory owned by the handle (48 N bytes
+ * per step; the checkpoints of the adjoint), so that mdpd_window_vjp_dev can
+ * run the chain rule backwards.  Reflection is not differentiable: handles
+ * with walls or a non-periodic axis are refused.  The window stays valid
+ * until the state, step index or parameters change (mdpd_step,
+ * mdpd_set_state*, mdpd_set_step, mdpd_set_params, mdpd_batch_set_params).
+ * Errors: INVALID_ARG, OOM, CUDA and the errors of mdpd_step.  Synchronises. */
+int mdpd_window_forward(mdpd_handle* h, int32_t nsteps);
+
+/* Adjoint of the recorded window (Algorithm 1 run backwards with the VJP of
+ * each step's force evaluation, random draws fixed): given the adjoints of
+ * the final state, xbar and vbar (device, 3N doubles, id order), and of the
+ * final evaluation's virial and local densities (what mdpd_observables /
+ * mdpd_batch_observables and mdpd_get_state report after the window), cvir
+ * (device, 6 doubles per replica) and rhobar (device, N doubles) -- each NULL
+ * for zero -- it returns x0bar, v0bar (device, 3N; may be NULL), the gradient with
+ * respect to the window's initial positions and velocities, and theta_bar
+ * (device, 3*8*8 doubles per replica; may be NULL), the gradient with
+ * respect to A, B, gamma as in mdpd_eval_vjp_dev, every step's and every
+ * replica's partials reduced in a fixed order.  Per step, with
+ * (xb, vb, ab) the adjoints of (x_{k+1}, v_{k+1}, a_{k+1}) and h = dt/2:
+ *   vhb = vb, ab += h vb;  xb += F_x^T ab, vhb += F_u^T ab;
+ *   vhb += dt xb;  vb = vhb, ab = h vhb   (frozen particles: no kick, no drift)
+ * and finally a_0 = F(x_0, v_0).  Afterwards the handle is back at the start
+ * of the window (x_0, v_0, step index s0, accelerations re-evaluated) and the
+ * window stays recorded, so it may be run again or differentiated with other
+ * adjoints.  Errors: INVALID_ARG (no recorded window), TILE_OVERFLOW, CUDA.
+ * Synchronises. */
+int mdpd_window_vjp_dev(mdpd_handle* h, const double* xbar, const double* vbar,
+                        const double* cvir, const double* rhobar, double* x0bar, double* v0bar,
+                        double* theta_bar);
 
 /* Time the density-pass variants (MDPD_KERNELS_NLIST, MDPD_KERNELS_NLIST_THREAD
  * in both code shapes of MDPD_OPT_DENSITY_SHAPE) and then the force pass at 1,

@@ -35,8 +35,10 @@ def window_forward(o: "O.Oracle", nsteps: int):
     return ck
 
 
-def window_vjp(o: "O.Oracle", ck, xbar, vbar):
-    """(xbar_0, vbar_0, tbar) of the window recorded in ck.
+def window_vjp(o: "O.Oracle", ck, xbar, vbar, cvir=None, rhobar=None):
+    """(xbar_0, vbar_0, tbar) of the window recorded in ck.  cvir and rhobar
+    (optional) are the adjoints of the conservative virial and of the local
+    densities of the window's last force evaluation, a_K = F(x_K, v'_{K-1}).
 
     Reverse sweep, with (xb, vb, ab) the adjoints of (x_{k+1}, v_{k+1}, a_{k+1}):
       v_{k+1} = v'_k + h a_{k+1}  ->  vhb = vb,  ab += h vb
@@ -53,10 +55,13 @@ def window_vjp(o: "O.Oracle", ck, xbar, vbar):
     vb = np.array(vbar, dtype=float)
     ab = np.zeros_like(xb)
     tb = np.zeros((3, 8, 8))
-    for k in range(len(ck["x"]) - 1, -1, -1):
+    K = len(ck["x"])
+    for k in range(K - 1, -1, -1):
         vhb = vb.copy()
         ab = ab + h * vb * mob
-        gx, gu, gt = o.force_vjp(ab, x=ck["x"][k], u=ck["vh"][k], step=ck["s0"] + k + 1)
+        last = k == K - 1
+        gx, gu, gt = o.eval_vjp(ab, cvir if last else None, rhobar if last else None,
+                                x=ck["x"][k], u=ck["vh"][k], step=ck["s0"] + k + 1)
         xb = xb + gx
         vhb = vhb + gu
         tb += gt

@@ -632,13 +632,17 @@ int orc_forces_subset(const orc_sys *s, int64_t n, const double *x, const double
 }
 
 /* ------------------------------------------------------------------------ */
-/* Vector-Jacobian product of one force evaluation.                          */
-/* The force evaluation maps (x, u, theta) to a_i = sum_j f_ij for mobile i   */
-/* (Sec. 2.1, Eq. 1), with rho_i = sum_j w_rho(r_ij) recomputed from x and u  */
-/* the velocities the dissipative term sees.  Given abar (3n), it returns     */
-/* xbar = (da/dx)^T abar, ubar = (da/du)^T abar and tbar[3][8][8], the        */
-/* gradient of L = sum_i abar_i . a_i with respect to the symmetric           */
-/* parameters A, B, gamma (entry [a][b] = [b][a] = dL/dP_ab).  The random     */
+/* Vector-Jacobian product of one evaluation.                                */
+/* The evaluation maps (x, u, theta) to the accelerations a_i = sum_j f_ij of */
+/* mobile i (Sec. 2.1, Eq. 1), to the conservative virial                     */
+/* W_ab = 1/2 sum_{i mobile} sum_j d_a F^C_b (the pressure tensor of Sec.     */
+/* 4.1) and to the local densities rho_i = sum_j w_rho(r_ij) (Sec. 2.1), with */
+/* u the velocities the dissipative term sees.  Given abar (3n), cvir (the    */
+/* six weights of W in the order xx yy zz xy xz yz) and rhobar (n), each may   */
+/* be NULL for zero, it returns the gradient of                               */
+/*   L = sum_i abar_i . a_i + sum_k cvir_k W_k + sum_i rhobar_i rho_i         */
+/* with respect to x (xbar), u (ubar) and the symmetric parameters A, B,      */
+/* gamma (tbar[3][8][8], entry [a][b] = [b][a] = dL/dP_ab).  The random       */
 /* draws xi_ij of the given step are held fixed.  Written from the chain rule */
 /* on each ordered pair (i mobile, j): with d = x_i - x_j, r = |d|, e = d/r,  */
 /* w = e.u_ij and f_ij = s e,                                                  */
@@ -646,12 +650,28 @@ int orc_forces_subset(const orc_sys *s, int64_t n, const double *x, const double
 /*       + sigma wc xi / sqrt(dt),                                             */
 /*   d(abar_i.f_ij)/dd = (abar_i.e)(s_r e + s_w (u_ij - w e)/r)               */
 /*                       + s (abar_i - (abar_i.e) e)/r,                        */
-/* s_r the r-derivative of s at fixed w and rho, s_w = -gamma wc^2; then the   */
-/* density chain rho_bar_k = dL/drho_k sent back through w_rho'(r) e.          */
+/* s_r the r-derivative of s at fixed w and rho, s_w = -gamma wc^2; the       */
+/* virial term of the pair, 1/2 (s_c / r) Q(d) with s_c = A wc + B (rho_i +   */
+/* rho_j) wd and Q(d) = sum_k cvir_k d_a d_b, has the d-gradient              */
+/*   1/2 [ (Q/r) s_c' e + s_c (grad Q / r - Q d / r^3) ];                      */
+/* then the density chain rho_bar_k = dL/drho_k sent back through w_rho'(r) e.*/
 /* ------------------------------------------------------------------------ */
+int orc_eval_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
+                 const int32_t *type, const uint32_t *id, uint64_t step,
+                 const double *abar, const double *cvir, const double *rhobar,
+                 double *xbar, double *ubar, double *tbar);
+
 int orc_force_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
                   const int32_t *type, const uint32_t *id, uint64_t step,
                   const double *abar, double *xbar, double *ubar, double *tbar)
+{
+    return orc_eval_vjp(s, n, x, u, type, id, step, abar, NULL, NULL, xbar, ubar, tbar);
+}
+
+int orc_eval_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
+                 const int32_t *type, const uint32_t *id, uint64_t step,
+                 const double *abar, const double *cvir, const double *rhobar,
+                 double *xbar, double *ubar, double *tbar)
 {
     double *rho = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *rbar = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
@@ -659,6 +679,7 @@ int orc_force_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
     if (orc_density(s, n, x, rho) != 0) { free(rho); free(rbar); return -1; }
     for (int64_t k = 0; k < 3 * n; ++k) { xbar[k] = 0.0; ubar[k] = 0.0; }
     for (int k = 0; k < 3 * ORC_MAXT * ORC_MAXT; ++k) tbar[k] = 0.0;
+    if (rhobar) for (int64_t k = 0; k < n; ++k) rbar[k] = rhobar[k];
     const double rc = s->rc, rd = s->rd;
     const double sq_dt = sqrt(s->dt);
     const double pi = 3.14159265358979323846264338327950288;
@@ -666,7 +687,8 @@ int orc_force_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
     /* force part (serial, plain) */
     for (int64_t i = 0; i < n; ++i) {
         if (is_frozen(s, type[i])) continue;
-        const double *ab = &abar[3 * i];
+        const double zero3[3] = { 0.0, 0.0, 0.0 };
+        const double *ab = abar ? &abar[3 * i] : zero3;
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
             double d[3];
@@ -708,6 +730,27 @@ int orc_force_vjp(const orc_sys *s, int64_t n, const double *x, const double *u,
             tbar[0 * 64 + a * 8 + b] += gA;
             tbar[1 * 64 + a * 8 + b] += gB;
             tbar[2 * 64 + a * 8 + b] += gG;
+            if (cvir) {
+                /* virial term 1/2 (s_c / r) Q(d) of this ordered pair */
+                double Q = cvir[0] * d[0] * d[0] + cvir[1] * d[1] * d[1] + cvir[2] * d[2] * d[2]
+                           + cvir[3] * d[0] * d[1] + cvir[4] * d[0] * d[2] + cvir[5] * d[1] * d[2];
+                double gQ[3] = { 2.0 * cvir[0] * d[0] + cvir[3] * d[1] + cvir[4] * d[2],
+                                 2.0 * cvir[1] * d[1] + cvir[3] * d[0] + cvir[5] * d[2],
+                                 2.0 * cvir[2] * d[2] + cvir[4] * d[0] + cvir[5] * d[1] };
+                double sc = A * wc + B * (rho[i] + rho[j]) * wd;
+                double sc_r = -A / rc - (near ? B * (rho[i] + rho[j]) / rd : 0.0);
+                for (int k = 0; k < 3; ++k) {
+                    double gd = 0.5 * ((Q / r) * sc_r * e[k] + sc * (gQ[k] / r - Q * d[k] / (r2 * r)));
+                    xbar[3 * i + k] += gd;
+                    xbar[3 * j + k] -= gd;
+                }
+                if (near) {
+                    rbar[i] += 0.5 * (Q / r) * B * wd;
+                    rbar[j] += 0.5 * (Q / r) * B * wd;
+                }
+                tbar[0 * 64 + a * 8 + b] += 0.5 * (Q / r) * wc;
+                tbar[1 * 64 + a * 8 + b] += 0.5 * (Q / r) * (rho[i] + rho[j]) * wd;
+            }
         }
     }
     /* density part: rho_k = sum_m w_rho(r_km) */

@@ -72,6 +72,7 @@ def lib():
         _lib.orc_set_num_threads.restype = None
         _lib.orc_forces_subset.argtypes = [P, i64, P, P, P, P, P, u64, i64, P, P]
         _lib.orc_force_vjp.argtypes = [P, i64, P, P, P, P, u64, P, P, P, P]
+        _lib.orc_eval_vjp.argtypes = [P, i64, P, P, P, P, u64, P, P, P, P, P, P]
     return _lib
 
 
@@ -261,6 +262,27 @@ class Oracle:
         if lib().orc_force_vjp(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(u), _ptr(self.type),
                                _ptr(self.ids), int(step), _ptr(ab), _ptr(xb), _ptr(ub),
                                _ptr(tb)) != 0:
+            raise RuntimeError("oracle vjp failed")
+        return xb, ub, tb
+
+    def eval_vjp(self, abar=None, cvir=None, rhobar=None, x=None, u=None, step=None):
+        """(xbar, ubar, tbar) of L = sum_i abar_i . a_i + sum_k cvir_k W_k +
+        sum_i rhobar_i rho_i (accelerations, conservative virial in the order
+        xx yy zz xy xz yz, local densities) at a fixed random stream; any of
+        the three cotangents may be None."""
+        x = self.x if x is None else _c(x, np.float64)
+        u = self.v if u is None else _c(u, np.float64)
+        step = self.step if step is None else step
+        ab = None if abar is None else _c(abar, np.float64)
+        cv = None if cvir is None else _c(cvir, np.float64)
+        rb = None if rhobar is None else _c(rhobar, np.float64)
+        xb = np.zeros_like(x)
+        ub = np.zeros_like(x)
+        tb = np.zeros((3, MAXT, MAXT))
+        if lib().orc_eval_vjp(C.byref(self.sys), x.shape[0], _ptr(x), _ptr(u), _ptr(self.type),
+                              _ptr(self.ids), int(step), None if ab is None else _ptr(ab),
+                              None if cv is None else _ptr(cv), None if rb is None else _ptr(rb),
+                              _ptr(xb), _ptr(ub), _ptr(tb)) != 0:
             raise RuntimeError("oracle vjp failed")
         return xb, ub, tb
 

@@ -1,22 +1,24 @@
-"""Gradients through short velocity-Verlet windows of the mDPD dynamics.
+"""Differentiable mDPD: gradients through velocity-Verlet windows and through
+one evaluation, for single systems and batches of replicas.
 
 `window(system, params, x0, v0, A, B, gamma, nsteps, step0)` advances the
-library's system `nsteps` steps from (x0, v0) with the pair tables A, B, gamma
-and returns (x_K, v_K) as a differentiable function of (x0, v0, A, B, gamma):
-`torch.autograd.Function` whose backward undoes the steps in reverse with the
-library's force vector-Jacobian product (`mdpd_force_vjp_dev`, hand-written
-CUDA kernels), the random stream of every step held fixed.  The forward keeps
-the positions and half-step velocities of every step (step checkpoints).
+system `nsteps` steps of Algorithm 1 from (x0, v0) with the pair tables A, B,
+gamma and returns (x_K, v_K) -- or, with `observables=True`, also the final
+evaluation's local densities rho_K (Sec. 2.1) and conservative virial W_K
+(six components per replica, the pressure tensor's interaction part of Sec.
+4.1) -- as a differentiable function of (x0, v0, A, B, gamma).  The forward
+records the window's checkpoints in the library (`mdpd_window_forward`); the
+backward runs the window's chain rule in reverse with one force VJP per step,
+the random stream of every step held fixed (`mdpd_window_vjp_dev`).  Every
+step of the method, forward and backward, runs in the library's kernels; this
+module only moves tensors between torch.autograd and the C ABI.
 
-The chain rule per step, with (xb, vb, ab) the adjoints of
-(x_{k+1}, v_{k+1}, a_{k+1}) and h = dt/2:
-    v_{k+1} = v'_k + h a_{k+1}   ->  vhb = vb,  ab += h vb
-    a_{k+1} = F(x_{k+1}, v'_k)   ->  xb += F_x^T ab, vhb += F_u^T ab, theta_bar += F_theta^T ab
-    x_{k+1} = x_k + dt v'_k      ->  vhb += dt xb
-    v'_k = v_k + h a_k           ->  vb = vhb, ab = h vhb
-and finally a_0 = F(x_0, v_0).  Frozen particles neither kick nor drift.
-Reflection off walls is not differentiable; systems with a wall mask are
-refused.  The system's state is overwritten by the backward pass.
+For a single system A, B, gamma are (8, 8) tables and W_K is (6,); for a
+batch (a `mdpd.Batch`) they are (nrep, 8, 8) and (nrep, 6), and `params` is
+the list of the replicas' parameters (only their tables are replaced).
+Reflection off walls or non-periodic faces is not differentiable; such
+systems are refused.  After the backward the system is back at the start of
+the window.
 """
 from __future__ import annotations
 
@@ -26,81 +28,106 @@ import torch
 from . import mdpd as M
 
 
-def _mobile_mask(system, params, device):
-    _, _, typ, _ = system.state()
-    mob = np.array([((params.frozen_mask >> int(t)) & 1) == 0 for t in typ], dtype=np.float64)
-    return torch.tensor(mob, device=device).unsqueeze(1)
+def _is_batch(system) -> bool:
+    return isinstance(system, M.Batch)
 
 
-def force_vjp(system, abar: torch.Tensor):
-    """(xbar, ubar, theta_bar) of one force evaluation at the system's current
-    positions, velocities and step index."""
-    xb = torch.zeros_like(abar)
-    ub = torch.zeros_like(abar)
-    tb = torch.zeros((3, 8, 8), dtype=torch.float64, device=abar.device)
-    M.mdpd_force_vjp_dev(system.h, abar.contiguous(), xb, ub, tb)
-    return xb, ub, tb
+def _set_tables(system, params, A, B, G):
+    """Write the tables A, B, gamma into the handle's parameters."""
+    if _is_batch(system):
+        ps = []
+        for r, p in enumerate(params):
+            q = p.copy()
+            q.A = A[r].detach().double().cpu().numpy().copy()
+            q.B = B[r].detach().double().cpu().numpy().copy()
+            q.gamma = G[r].detach().double().cpu().numpy().copy()
+            ps.append(q)
+        M.mdpd_batch_set_params(system.h, ps)
+    else:
+        q = params.copy()
+        q.A = A.detach().double().cpu().numpy().copy()
+        q.B = B.detach().double().cpu().numpy().copy()
+        q.gamma = G.detach().double().cpu().numpy().copy()
+        M.mdpd_set_params(system.h, q)
 
 
-def _vjp_at(system, x, u, step, abar):
-    M.mdpd_set_step(system.h, step)
-    M.mdpd_set_state_dev(system.h, x.contiguous(), u.contiguous())
-    return force_vjp(system, abar)
+def _virial(system, device):
+    """Conservative virial of the last evaluation, (6,) or (nrep, 6)."""
+    if _is_batch(system):
+        obs = M.mdpd_batch_observables(system.h, False, False)
+        return torch.tensor(np.ascontiguousarray(obs[:, 5:11]), dtype=torch.float64, device=device)
+    obs = M.mdpd_observables(system.h)
+    return torch.tensor(np.ascontiguousarray(obs[5:11]), dtype=torch.float64, device=device)
+
+
+def _opt(t):
+    """A contiguous cotangent, or None (zero) when autograd passes none."""
+    return t.contiguous() if t is not None else None
 
 
 class _Window(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x0, v0, A, B, G, system, params, nsteps, step0):
-        if getattr(system, "has_walls", False):
-            raise ValueError("reflection off walls is not differentiable")
-        p = params.copy()
-        p.A = A.detach().double().cpu().numpy().copy()
-        p.B = B.detach().double().cpu().numpy().copy()
-        p.gamma = G.detach().double().cpu().numpy().copy()
         h = system.h
-        M.mdpd_set_params(h, p)
+        _set_tables(system, params, A, B, G)
         M.mdpd_set_step(h, step0)
         M.mdpd_set_state_dev(h, x0.detach().contiguous(), v0.detach().contiguous())
-        mob = _mobile_mask(system, p, x0.device)
-        hdt = 0.5 * p.dt
-        a = torch.empty_like(x0)
-        M.mdpd_get_accel_dev(h, a)
-        v = v0.detach()
-        xs, vhs = [], []
-        x = x0.detach()
-        for _ in range(nsteps):
-            vhs.append(v + hdt * a * mob)
-            M.mdpd_step(h, 1)
-            x = torch.empty_like(x0)
-            v = torch.empty_like(v0)
-            M.mdpd_get_state_dev(h, x, v)
-            M.mdpd_get_accel_dev(h, a)
-            xs.append(x)
-        ctx.system, ctx.params, ctx.step0, ctx.mob = system, p, step0, mob
-        ctx.x0, ctx.v0, ctx.xs, ctx.vhs = x0.detach(), v0.detach(), xs, vhs
-        return x.clone(), v.clone()
+        M.mdpd_window_forward(h, nsteps)
+        x = torch.empty_like(x0)
+        v = torch.empty_like(v0)
+        rho = torch.empty(x0.shape[0], dtype=torch.float64, device=x0.device)
+        M.mdpd_get_state_dev(h, x, v, None, rho)
+        W = _virial(system, x0.device)
+        ctx.system = system
+        ctx.tshape = tuple(A.shape)
+        return x, v, rho, W
 
     @staticmethod
-    def backward(ctx, xbar, vbar):
-        system, p, s0, mob = ctx.system, ctx.params, ctx.step0, ctx.mob
-        h, dt = 0.5 * p.dt, p.dt
-        xb = xbar.double().clone() if xbar is not None else torch.zeros_like(ctx.x0)
-        vb = vbar.double().clone() if vbar is not None else torch.zeros_like(ctx.v0)
-        ab = torch.zeros_like(xb)
-        tb = torch.zeros((3, 8, 8), dtype=torch.float64, device=xb.device)
-        for k in range(len(ctx.xs) - 1, -1, -1):
-            vhb = vb.clone()
-            ab = ab + h * vb * mob
-            gx, gu, gt = _vjp_at(system, ctx.xs[k], ctx.vhs[k], s0 + k + 1, ab)
-            xb = xb + gx
-            vhb = vhb + gu
-            tb = tb + gt
-            vhb = vhb + dt * xb * mob
-            vb = vhb
-            ab = h * vhb * mob
-        gx, gu, gt = _vjp_at(system, ctx.x0, ctx.v0, s0, ab)
-        xb, vb, tb = xb + gx, vb + gu, tb + gt
-        return xb, vb, tb[0], tb[1], tb[2], None, None, None, None
+    def backward(ctx, xbar, vbar, rhobar, wbar):
+        system = ctx.system
+        h = system.h
+        like = torch.empty((system.n, 3), dtype=torch.float64, device=(
+            xbar if xbar is not None else vbar if vbar is not None else rhobar
+            if rhobar is not None else wbar).device)
+        x0b = torch.empty_like(like)
+        v0b = torch.empty_like(like)
+        nrep = system.nrep if _is_batch(system) else 1
+        tb = torch.empty((nrep, 3, 8, 8), dtype=torch.float64, device=like.device)
+        M.mdpd_window_vjp_dev(h, _opt(xbar), _opt(vbar), _opt(wbar), _opt(rhobar), x0b, v0b, tb)
+        if _is_batch(system):
+            gA, gB, gG = tb[:, 0], tb[:, 1], tb[:, 2]
+        else:
+            gA, gB, gG = tb[0, 0], tb[0, 1], tb[0, 2]
+        return x0b, v0b, gA, gB, gG, None, None, None, None
+
+
+def window(system, params, x0, v0, A, B, gamma, nsteps: int, step0: int = 0,
+           observables: bool = False):
+    """Differentiable (x_K, v_K) after nsteps velocity-Verlet steps, and with
+    observables=True also (rho_K, W_K) of the last evaluation (see module)."""
+    x, v, rho, W = _Window.apply(x0, v0, A, B, gamma, system, params, int(nsteps), int(step0))
+    return (x, v, rho, W) if observables else (x, v)
+
+
+def eval_vjp(system, abar=None, cvir=None, rhobar=None):
+    """(xbar, ubar, theta_bar) of one evaluation at the system's current
+    state (mdpd_eval_vjp_dev): L = sum abar . a + sum cvir . W + sum rhobar rho."""
+    ref = next(t for t in (abar, cvir, rhobar) if t is not None)
+    n = system.n
+    nrep = system.nrep if _is_batch(system) else 1
+    xb = torch.empty((n, 3), dtype=torch.float64, device=ref.device)
+    ub = torch.empty_like(xb)
+    tb = torch.empty((nrep, 3, 8, 8), dtype=torch.float64, device=ref.device)
+    M.mdpd_eval_vjp_dev(system.h, None if abar is None else abar.contiguous(),
+                        None if cvir is None else cvir.contiguous(),
+                        None if rhobar is None else rhobar.contiguous(), xb, ub, tb)
+    return xb, ub, (tb if _is_batch(system) else tb[0])
+
+
+def force_vjp(system, abar: torch.Tensor):
+    """(xbar, ubar, theta_bar) of one force evaluation at the system's current
+    positions, velocities and step index."""
+    return eval_vjp(system, abar=abar)
 
 
 class _Density(torch.autograd.Function):
@@ -129,8 +156,3 @@ def density(system, x):
     through its vector-Jacobian product (mdpd_density_vjp_dev).  The system's
     state is overwritten (positions x, velocities zero)."""
     return _Density.apply(x, system)
-
-
-def window(system, params, x0, v0, A, B, gamma, nsteps: int, step0: int = 0):
-    """Differentiable (x_K, v_K) after nsteps velocity-Verlet steps (see module)."""
-    return _Window.apply(x0, v0, A, B, gamma, system, params, int(nsteps), int(step0))

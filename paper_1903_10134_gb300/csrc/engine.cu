@@ -118,12 +118,29 @@ struct mdpd_handle {
     int4* d_cchunks = nullptr;
     int2* d_wr = nullptr;
     double* obs_b = nullptr;
+    Rep* d_reps_all = nullptr;       // the same records with list_all set (adjoint lists)
     int nchunk = 0, ncchunk = 0;
 
-    Batch batch() const
+    // adjoint: per-block parameter partials and per-replica sums, virial
+    // weights, and a velocity-Verlet window's checkpoints (id order:
+    // x_0..x_K, v'_0..v'_{K-1}, v_0) and reverse-sweep vectors (xb, vb, ab)
+    double* vjp_tpart = nullptr;
+    double* vjp_tacc = nullptr;
+    double* vjp_wbar = nullptr;
+    double* win_x = nullptr;
+    double* win_vh = nullptr;
+    double* win_v0 = nullptr;
+    double* win_b = nullptr;
+    int64_t win_alloc_steps = 0;     // steps the checkpoint arrays hold
+    size_t win_vec = 0;              // 3N they were sized for
+    int vjp_nblk = 0;                // blocks vjp_tpart was sized for
+    int64_t win_k = 0, win_s0 = 0;
+    bool win_valid = false;
+
+    Batch batch(bool all = false) const
     {
         Batch b;
-        b.reps = d_reps;
+        b.reps = all && d_reps_all ? d_reps_all : d_reps;
         b.chunks = d_chunks;
         b.cchunks = d_cchunks;
         b.nchunk = nchunk;
@@ -480,15 +497,17 @@ void ensure_ff(mdpd_handle* h)
     h->ff_dirty = false;
 }
 
-void enqueue_density(mdpd_handle* h)
+// all: partner lists for every particle, frozen ones too (the adjoint's;
+// a single system takes it from ph.list_all).
+void enqueue_density(mdpd_handle* h, bool all = false)
 {
     const bool cell = h->kernels == MDPD_KERNELS_NLIST;
     if (h->nrep) {
         if (cell)
-            launch_density_cell_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
+            launch_density_cell_batch(h->stream, h->precision, h->cap, h->batch(all), h->pos4,
                                       h->start, h->rho, h->nl, h->nl_count);
         else
-            launch_density_nl_batch(h->stream, h->precision, h->cap, h->batch(), h->pos4,
+            launch_density_nl_batch(h->stream, h->precision, h->cap, h->batch(all), h->pos4,
                                     h->cell_s, h->start, h->rho, h->nl, h->nl_count,
                                     h->thread_shape);
         return;
@@ -847,6 +866,18 @@ int create_common(const mdpd_params* params, int64_t n, const double* pos, const
     return init_handle(h, pos, vel, type, stream, device_inputs, { 0, n }, { params->ntypes }, out);
 }
 
+// The device copies of the replica records: as they are, and with list_all
+// set (the adjoint's partner lists cover frozen particles too).
+int upload_reps(mdpd_handle* h)
+{
+    const size_t bytes = sizeof(Rep) * (size_t)h->nrep;
+    CK(cudaMemcpy(h->d_reps, h->reps.data(), bytes, cudaMemcpyHostToDevice));
+    std::vector<Rep> all(h->reps);
+    for (auto& R : all) R.ph.list_all = 1;
+    CK(cudaMemcpy(h->d_reps_all, all.data(), bytes, cudaMemcpyHostToDevice));
+    return MDPD_OK;
+}
+
 // Batch of nrep independent systems: replica r has its own parameters, seed
 // and n[r] particles (the ids [sum_{q<r} n[q], ... + n[r]) of the inputs); its
 // cells follow those of replica r - 1 in one lattice, so one launch of each
@@ -921,6 +952,7 @@ int create_batch(int32_t nrep, const mdpd_params* params, const int64_t* n, cons
     h->ncchunk = (int)cchunks.size();
     int rc;
     if ((rc = dalloc(h, &h->d_reps, sizeof(Rep) * (size_t)nrep)) ||
+        (rc = dalloc(h, &h->d_reps_all, sizeof(Rep) * (size_t)nrep)) ||
         (rc = dalloc(h, &h->d_chunks, sizeof(int4) * chunks.size())) ||
         (rc = dalloc(h, &h->d_cchunks, sizeof(int4) * cchunks.size())) ||
         (rc = dalloc(h, &h->d_wr, sizeof(int2) * wr.size())) ||
@@ -929,7 +961,7 @@ int create_batch(int32_t nrep, const mdpd_params* params, const int64_t* n, cons
         mdpd_destroy(h);
         return rc;
     }
-    bool ok = cudaMemcpy(h->d_reps, h->reps.data(), sizeof(Rep) * (size_t)nrep, cudaMemcpyHostToDevice) == cudaSuccess &&
+    bool ok = upload_reps(h) == MDPD_OK &&
               (chunks.empty() || cudaMemcpy(h->d_chunks, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
               (cchunks.empty() || cudaMemcpy(h->d_cchunks, cchunks.data(), sizeof(int4) * cchunks.size(), cudaMemcpyHostToDevice) == cudaSuccess) &&
               cudaMemcpy(h->d_wr, wr.data(), sizeof(int2) * wr.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -1030,8 +1062,8 @@ int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params)
         h->rep_p[r] = params[r];
     }
     // the records live in device memory: captured graphs stay valid
-    CK(cudaMemcpy(h->d_reps, h->reps.data(), sizeof(Rep) * (size_t)h->nrep, cudaMemcpyHostToDevice));
-    return MDPD_OK;
+    h->win_valid = false;
+    return upload_reps(h);
 }
 
 int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny, int32_t nz,
@@ -1041,6 +1073,7 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "walls are not supported on a batch handle");
     if (h->walls_set) return h->fail(MDPD_ERR_INVALID_ARG, "walls already set");
+    h->win_valid = false;
     if (!solid || !origin || nx <= 0 || ny <= 0 || nz <= 0 || !(voxel > 0) || !is_fin(voxel))
         return h->fail(MDPD_ERR_INVALID_ARG, "bad mask dimensions or voxel size");
     if (wall_type < 0 || wall_type >= h->p.ntypes)
@@ -1182,6 +1215,7 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return MDPD_OK;
+    h->win_valid = false;
     ensure_ff(h);
     // the first step's binning applies the first half-kick and drift; later
     // steps get them from the previous force pass (FM_FUSED)
@@ -1285,6 +1319,7 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
     int rc = sync_check(h);
     if (rc) return rc;
     if (dev && ((rc = check_ptr_kind(h, pos, true)) || (rc = check_ptr_kind(h, vel, true)))) return rc;
+    h->win_valid = false;
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
     const int c = h->cur;
@@ -1519,6 +1554,7 @@ int mdpd_set_params(mdpd_handle* h, const mdpd_params* p)
         p->ntypes != h->p.ntypes)
         return h->fail(MDPD_ERR_INVALID_ARG, "rc, rd, precision and ntypes cannot change");
     if ((rc = sync_check(h))) return rc;
+    h->win_valid = false;
     h->p = *p;
     setup_geo_phys(h);
     h->ff_dirty = true;                      // r_d or the frozen types may change
@@ -1532,6 +1568,7 @@ int mdpd_set_step(mdpd_handle* h, int64_t step)
     int rc = sync_check(h);
     if (rc) return rc;
     const uint64_t s = (uint64_t)step;
+    h->win_valid = false;
     CK(cudaMemcpy(h->step, &s, sizeof(s), cudaMemcpyHostToDevice));
     h->steps_host = step;
     return MDPD_OK;
@@ -1548,68 +1585,239 @@ int mdpd_get_accel_dev(mdpd_handle* h, double* accel)
     return sync_check(h);
 }
 
-int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
-                       double* theta_bar)
+// ---- adjoint ---------------------------------------------------------------------
+
+namespace {
+
+int vjp_nrep(const mdpd_handle* h) { return h->nrep ? h->nrep : 1; }
+
+// Parameter partials sized for the current particle count (which grows when
+// walls are added).
+int vjp_alloc(mdpd_handle* h)
+{
+    const Batch bt = h->batch();
+    const int nblk = std::max(1, vjp_num_blocks((int)h->n, h->nrep ? &bt : nullptr));
+    if (h->vjp_tpart && h->vjp_nblk >= nblk) return MDPD_OK;
+    dfree(h->vjp_tpart);
+    dfree(h->vjp_tacc);
+    dfree(h->vjp_wbar);
+    h->vjp_nblk = 0;
+    int rc;
+    if ((rc = dalloc(h, &h->vjp_tpart, (size_t)nblk * THETA_SLOTS * sizeof(double))) ||
+        (rc = dalloc(h, &h->vjp_tacc, (size_t)vjp_nrep(h) * THETA_SLOTS * sizeof(double))) ||
+        (rc = dalloc(h, &h->vjp_wbar, (size_t)vjp_nrep(h) * 6 * sizeof(double))))
+        return rc;
+    h->vjp_nblk = nblk;
+    return MDPD_OK;
+}
+
+// Cell order and partner lists of every particle (frozen ones included) for
+// the state in the master arrays: a binning and a density pass, no forces.
+void vjp_prepare(mdpd_handle* h, bool gather_a)
+{
+    h->ph.list_all = 1;
+    enqueue_bin(h, gather_a);
+    enqueue_density(h, true);
+    h->ph.list_all = 0;
+}
+
+// One VJP of the evaluation prepared by vjp_prepare: the force/virial part,
+// the caller's density adjoint (id order, may be NULL) added to the density
+// chain, the density chain, and the parameter partials summed per replica
+// into vjp_tacc (stored, or added when add_theta).  Outputs in cell order in
+// the spare master buffers: xbar in x[1 - cur], ubar in v[1 - cur].
+void vjp_core(mdpd_handle* h, const double* abar, const double* wbar, const double* rhobar,
+              int add_theta)
+{
+    cudaStream_t st = h->stream;
+    const int n = (int)h->n;
+    const int c = h->cur;
+    const Batch bt = h->batch(true);
+    const Batch* pb = h->nrep ? &bt : nullptr;
+    double* xs = h->x[1 - c];
+    double* us = h->v[1 - c];
+    double* rs = h->a[1 - c];
+    launch_force_vjp(st, h->precision, n, h->cap, h->ph, pb, h->pos4, h->vel4, h->rho, h->nl,
+                     h->nl_count, h->step, abar, wbar, xs, us, rs, h->vjp_tpart, h->status);
+    if (rhobar) launch_gather_by_id(st, n, h->id[c], rhobar, rs, 1);
+    launch_density_vjp(st, h->precision, n, h->cap, h->ph, pb, h->pos4, h->nl, h->nl_count, rs,
+                       xs, h->status);
+    launch_theta_reduce(st, vjp_nrep(h), vjp_num_blocks(n, pb), h->nrep ? h->d_wr : nullptr,
+                        PAIR_BLOCK_WARPS, h->vjp_tpart, h->vjp_tacc, add_theta);
+}
+
+// Master state from device arrays in id order (no evaluation).
+void load_state_dev(mdpd_handle* h, const double* pos, const double* vel)
+{
+    if (h->nrep)
+        launch_load_state_batch(h->stream, h->cap, pos, vel, nullptr, h->batch(),
+                                master(h, h->cur), h->type_by_id, h->status);
+    else
+        launch_load_state(h->stream, (int)h->n, h->cap, pos, vel, nullptr, h->geo,
+                          master(h, h->cur), h->type_by_id, h->status);
+    h->ff_dirty = true;
+}
+
+// A window needs differentiable steps: no reflection off walls or
+// non-periodic faces.
+bool window_allowed(const mdpd_handle* h, std::string& why)
+{
+    if (h->mk.bits || h->walls_set) { why = "reflection off walls is not differentiable"; return false; }
+    const int nr = vjp_nrep(h);
+    for (int r = 0; r < nr; ++r) {
+        const mdpd_params& p = h->nrep ? h->rep_p[r] : h->p;
+        for (int k = 0; k < 3; ++k)
+            if (!p.periodic[k]) {
+                why = "reflection at a non-periodic face is not differentiable";
+                return false;
+            }
+    }
+    return true;
+}
+
+}  // namespace
+
+int mdpd_eval_vjp_dev(mdpd_handle* h, const double* abar, const double* cvir,
+                      const double* rhobar, double* xbar, double* ubar, double* theta_bar)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
     int rc = sync_check(h);
     if (rc) return rc;
-    if (!abar) return h->fail(MDPD_ERR_INVALID_ARG, "abar is required");
-    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "the force VJP is not available on a batch handle");
-    if ((rc = check_ptr_kind(h, abar, true)) || (rc = check_ptr_kind(h, xbar, true)) ||
+    if ((rc = check_ptr_kind(h, abar, true)) || (rc = check_ptr_kind(h, cvir, true)) ||
+        (rc = check_ptr_kind(h, rhobar, true)) || (rc = check_ptr_kind(h, xbar, true)) ||
         (rc = check_ptr_kind(h, ubar, true)) || (rc = check_ptr_kind(h, theta_bar, true)))
         return rc;
+    if ((rc = vjp_alloc(h))) return rc;
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
-    h->ph.list_all = 1;                      // partners of frozen particles too
-    rc = evaluate(h, h->fout, true);
-    h->ph.list_all = 0;
-    if (rc) return rc;
+    vjp_prepare(h, true);
+    vjp_core(h, abar, cvir, rhobar, 0);
     const int c = h->cur;
-    double* xs = h->x[1 - c];                // scratch: [3][cap] each, rbar [cap]
-    double* us = h->v[1 - c];
-    double* rs = h->a[1 - c];
-    double* tb = theta_bar ? theta_bar : h->fout;
-    CK(cudaMemsetAsync(tb, 0, 3 * 64 * sizeof(double), st));
-    launch_force_vjp(st, h->precision, n, h->cap, h->geo, h->ph, h->pos4, h->vel4, h->rho, h->nl,
-                     h->nl_count, h->step, abar, xs, us, rs, tb, h->status);
-    if (xbar) launch_scatter_by_id(st, n, h->cap, h->id[c], xs, xbar);
-    if (ubar) launch_scatter_by_id(st, n, h->cap, h->id[c], us, ubar);
+    if (xbar) launch_scatter_by_id(st, n, h->cap, h->id[c], h->x[1 - c], xbar);
+    if (ubar) launch_scatter_by_id(st, n, h->cap, h->id[c], h->v[1 - c], ubar);
+    if (theta_bar) launch_theta_symmetrise(st, vjp_nrep(h), h->vjp_tacc, theta_bar);
     CK(cudaGetLastError());
-    rc = sync_check(h);
-    if (rc) return rc;
-    if (theta_bar) {
-        // symmetric parameters: mirror the a <= b entries
-        double t[3 * 64];
-        CK(cudaMemcpy(t, theta_bar, sizeof(t), cudaMemcpyDeviceToHost));
-        for (int q = 0; q < 3; ++q)
-            for (int a = 0; a < 8; ++a)
-                for (int b = a + 1; b < 8; ++b) t[q * 64 + b * 8 + a] = t[q * 64 + a * 8 + b];
-        CK(cudaMemcpy(theta_bar, t, sizeof(t), cudaMemcpyHostToDevice));
-    }
-    return MDPD_OK;
+    return sync_check(h);
+}
+
+int mdpd_force_vjp_dev(mdpd_handle* h, const double* abar, double* xbar, double* ubar,
+                       double* theta_bar)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (!abar) return h->fail(MDPD_ERR_INVALID_ARG, "abar is required");
+    return mdpd_eval_vjp_dev(h, abar, nullptr, nullptr, xbar, ubar, theta_bar);
 }
 
 int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar)
 {
     if (!h) return MDPD_ERR_INVALID_ARG;
+    if (!rhobar || !xbar) return h->fail(MDPD_ERR_INVALID_ARG, "rhobar and xbar are required");
+    return mdpd_eval_vjp_dev(h, nullptr, nullptr, rhobar, xbar, nullptr, nullptr);
+}
+
+int mdpd_window_forward(mdpd_handle* h, int32_t nsteps)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (nsteps < 1) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps must be >= 1");
+    std::string why;
+    if (!window_allowed(h, why)) return h->fail(MDPD_ERR_INVALID_ARG, why);
     int rc = sync_check(h);
     if (rc) return rc;
-    if (!rhobar || !xbar) return h->fail(MDPD_ERR_INVALID_ARG, "rhobar and xbar are required");
-    if (h->nrep) return h->fail(MDPD_ERR_INVALID_ARG, "the density VJP is not available on a batch handle");
-    if ((rc = check_ptr_kind(h, rhobar, true)) || (rc = check_ptr_kind(h, xbar, true))) return rc;
-    cudaStream_t st = h->stream;
+    flush_pending(h);
     const int n = (int)h->n;
-    h->ph.list_all = 1;                      // lists for every particle, frozen ones too
-    rc = evaluate(h, h->fout, true);
-    h->ph.list_all = 0;
+    const size_t vec = (size_t)std::max(n, 1) * 3;
+    if (h->win_alloc_steps < nsteps || h->win_vec != vec) {
+        dfree(h->win_x);
+        dfree(h->win_vh);
+        dfree(h->win_v0);
+        dfree(h->win_b);
+        h->win_alloc_steps = 0;
+        h->win_vec = 0;
+        if ((rc = dalloc(h, &h->win_x, vec * (size_t)(nsteps + 1) * sizeof(double))) ||
+            (rc = dalloc(h, &h->win_vh, vec * (size_t)nsteps * sizeof(double))) ||
+            (rc = dalloc(h, &h->win_v0, vec * sizeof(double))) ||
+            (rc = dalloc(h, &h->win_b, 3 * vec * sizeof(double))))
+            return rc;
+        h->win_alloc_steps = nsteps;
+        h->win_vec = vec;
+    }
+    h->win_valid = false;
+    cudaStream_t st = h->stream;
+    const Batch bt = h->batch();
+    const Batch* pb = h->nrep ? &bt : nullptr;
+    h->win_s0 = h->steps_host;
+    launch_win_record(st, n, h->cap, h->ph, pb, master(h, h->cur), h->win_x, nullptr);
+    launch_scatter_by_id(st, n, h->cap, h->id[h->cur], h->v[h->cur], h->win_v0);
+    for (int32_t k = 0; k < nsteps; ++k) {
+        launch_win_record(st, n, h->cap, h->ph, pb, master(h, h->cur), h->win_x + vec * k,
+                          h->win_vh + vec * k);
+        ensure_ff(h);
+        if ((rc = run_step(h, FM_LAST, true))) return rc;
+        ++h->steps_host;
+        launch_win_record(st, n, h->cap, h->ph, pb, master(h, h->cur), h->win_x + vec * (k + 1),
+                          nullptr);
+    }
+    CK(cudaGetLastError());
+    if ((rc = sync_check(h))) return rc;
+    h->win_k = nsteps;
+    h->win_valid = true;
+    return MDPD_OK;
+}
+
+int mdpd_window_vjp_dev(mdpd_handle* h, const double* xbar, const double* vbar,
+                        const double* cvir, const double* rhobar, double* x0bar, double* v0bar,
+                        double* theta_bar)
+{
+    if (!h) return MDPD_ERR_INVALID_ARG;
+    if (!h->win_valid) return h->fail(MDPD_ERR_INVALID_ARG, "no recorded window (mdpd_window_forward)");
+    int rc = sync_check(h);
     if (rc) return rc;
-    const int c = h->cur;
-    double* xs = h->x[1 - c];                // scratch: [3][cap]; rbar [cap]
-    double* rs = h->a[1 - c];
-    launch_density_vjp(st, h->precision, n, h->cap, h->geo, h->ph, h->pos4, h->nl, h->nl_count,
-                       h->id[c], rhobar, rs, xs, h->status);
-    launch_scatter_by_id(st, n, h->cap, h->id[c], xs, xbar);
+    if ((rc = check_ptr_kind(h, xbar, true)) || (rc = check_ptr_kind(h, vbar, true)) ||
+        (rc = check_ptr_kind(h, cvir, true)) || (rc = check_ptr_kind(h, rhobar, true)) ||
+        (rc = check_ptr_kind(h, x0bar, true)) || (rc = check_ptr_kind(h, v0bar, true)) ||
+        (rc = check_ptr_kind(h, theta_bar, true)))
+        return rc;
+    if ((rc = vjp_alloc(h))) return rc;
+    const int n = (int)h->n;
+    const size_t vec = (size_t)std::max(n, 1) * 3;
+    if (vec != h->win_vec) return h->fail(MDPD_ERR_INVALID_ARG, "the window was recorded for another particle count");
+    cudaStream_t st = h->stream;
+    flush_pending(h);
+    const Batch bt = h->batch();
+    const Batch* pb = h->nrep ? &bt : nullptr;
+    double* xb = h->win_b;
+    double* vb = h->win_b + vec;
+    double* ab = h->win_b + 2 * vec;
+    const int64_t K = h->win_k, s0 = h->win_s0;
+    launch_win_init(st, n, h->ph, pb, master(h, h->cur), xbar, vbar, xb, vb, ab);
+    // reverse sweep: the force evaluation of step k + 1 at (x_{k+1}, v'_k);
+    // the last one also produced the final densities and virial
+    for (int64_t k = K - 1; k >= 0; --k) {
+        load_state_dev(h, h->win_x + vec * (k + 1), h->win_vh + vec * k);
+        launch_set_step(st, h->step, (uint64_t)(s0 + k + 1));
+        vjp_prepare(h, false);
+        const bool last = k == K - 1;
+        vjp_core(h, ab, last ? cvir : nullptr, last ? rhobar : nullptr, last ? 0 : 1);
+        const int c = h->cur;
+        launch_win_post(st, n, h->cap, h->ph, pb, master(h, c), h->x[1 - c], h->v[1 - c], xb, vb,
+                        ab, k == 0 ? 1 : 0, 0, nullptr, nullptr);
+    }
+    // a_0 = F(x_0, v_0) at step s0
+    load_state_dev(h, h->win_x, h->win_v0);
+    launch_set_step(st, h->step, (uint64_t)s0);
+    vjp_prepare(h, false);
+    vjp_core(h, ab, nullptr, nullptr, 1);
+    {
+        const int c = h->cur;
+        launch_win_post(st, n, h->cap, h->ph, pb, master(h, c), h->x[1 - c], h->v[1 - c], xb, vb,
+                        ab, 0, 1, x0bar, v0bar);
+    }
+    if (theta_bar) launch_theta_symmetrise(st, vjp_nrep(h), h->vjp_tacc, theta_bar);
+    // the handle returns to the start of the window: (x_0, v_0), step s0,
+    // accelerations re-evaluated
+    load_state_dev(h, h->win_x, h->win_v0);
+    if ((rc = evaluate(h, nullptr, false))) return rc;
+    h->steps_host = s0;
     CK(cudaGetLastError());
     return sync_check(h);
 }
@@ -1730,6 +1938,14 @@ void mdpd_destroy(mdpd_handle* h)
     dfree(h->obs);
     dfree(h->mask_bits);
     dfree(h->d_reps);
+    dfree(h->d_reps_all);
+    dfree(h->vjp_tpart);
+    dfree(h->vjp_tacc);
+    dfree(h->vjp_wbar);
+    dfree(h->win_x);
+    dfree(h->win_vh);
+    dfree(h->win_v0);
+    dfree(h->win_b);
     dfree(h->d_chunks);
     dfree(h->d_cchunks);
     dfree(h->d_wr);

@@ -357,21 +357,47 @@ void launch_reduce_obs_batch(cudaStream_t st, int precision, const double* parti
                              uint64_t* step_ptr, int advance);
 
 // ---- launchers (adjoint) ---------------------------------------------------
+// All take bt = nullptr for a single system (blocks of PAIR_BLOCK slots) or a
+// batch (one block per chunk).  Vectors in id order are interleaved xyz;
+// cell-ordered outputs are component-major [3][cap].
+// Blocks of a VJP launch (entries of tpart / TB).
+int vjp_num_blocks(int n, const Batch* bt);
 // VJP of one force evaluation at the current cell-ordered state (lists built
-// with list_all); xbar, ubar component-major [3][cap], rbar [cap] scratch,
-// tbar [3][64] accumulated with atomics (zero it first).
-// VJP of the density pass alone: xbar (component-major [3][cap], zeroed here)
-// = d(sum_i rhobar_i rho_i)/dx for rhobar given in id order (rbar: [cap]
-// scratch), over the lists of the last density pass (built with list_all).
-void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
-                        const Phys& ph, const void* pos4, const uint32_t* nl,
-                        const uint32_t* nl_count, const uint32_t* id, const double* rhobar,
-                        double* rbar, double* xbar, uint32_t* status);
-void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
-                      const Phys& ph, const void* pos4, const void* vel4, const void* rho,
+// with list_all): abar (id order, may be NULL) the adjoint of the
+// accelerations, wbar (6 per replica, may be NULL) weights of the virial
+// components; xbar, ubar, rbar outputs in cell order; tpart[block][3 * 64]
+// the blocks' parameter partials by (parameter, own type, partner type).
+void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
+                      const Batch* bt, const void* pos4, const void* vel4, const void* rho,
                       const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,
-                      const double* abar, double* xbar, double* ubar, double* rbar, double* tbar,
-                      uint32_t* status);
+                      const double* abar, const double* wbar, double* xbar, double* ubar,
+                      double* rbar, double* tpart, uint32_t* status);
+// The density chain: xbar (cell order, [3][cap]) += sum_j (rbar_i + rbar_j)
+// w_rho'(r) e over partners within r_d (rbar in cell order).
+void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
+                        const Batch* bt, const void* pos4, const uint32_t* nl,
+                        const uint32_t* nl_count, const double* rbar, double* xbar,
+                        uint32_t* status);
+void launch_gather_by_id(cudaStream_t st, int n, const uint32_t* id, const double* in, double* out,
+                         int add);
+// *step_ptr = value, ordered on the stream.
+void launch_set_step(cudaStream_t st, uint64_t* step_ptr, uint64_t value);
+constexpr int THETA_SLOTS = 3 * 64;   // [parameter][type][type] of A, B, gamma
+// Per replica: acc[r] (= or +=) the sum of its blocks' partials in block
+// order; ranges[r] / scale = the replica's block range (NULL: all nblk).
+void launch_theta_reduce(cudaStream_t st, int nrep, int nblk, const int2* ranges, int scale,
+                         const double* tpart, double* acc, int add);
+// Symmetric-table gradient [r][3][8][8] from the per-type-pair sums.
+void launch_theta_symmetrise(cudaStream_t st, int nrep, const double* acc, double* out);
+// Window checkpoints, start of the reverse sweep, and one reverse step's
+// chain rule (see k_adjoint.cu).
+void launch_win_record(cudaStream_t st, int n, int64_t cap, const Phys& ph, const Batch* bt,
+                       const Master& m, double* X, double* VH);
+void launch_win_init(cudaStream_t st, int n, const Phys& ph, const Batch* bt, const Master& m,
+                     const double* xbar, const double* vbar, double* xb, double* vb, double* ab);
+void launch_win_post(cudaStream_t st, int n, int64_t cap, const Phys& ph, const Batch* bt,
+                     const Master& m, const double* gx, const double* gu, double* xb, double* vb,
+                     double* ab, int first, int final, double* x0bar, double* v0bar);
 
 // ---- launchers (walls) -----------------------------------------------------
 void launch_mask_pack(cudaStream_t st, const uint8_t* mask, int64_t nvox, uint32_t* bits);

@@ -99,7 +99,8 @@ SYMBOLS = (
     "mdpd_get_accel_dev", "mdpd_force_vjp_dev", "mdpd_get_wall_density", "mdpd_density_noalloc", "mdpd_destroy",
     "mdpd_last_error", "mdpd_create_batch", "mdpd_num_replicas", "mdpd_batch_observables",
     "mdpd_batch_set_params", "mdpd_measure_fma_peak", "mdpd_density_vjp_dev",
-    "mdpd_get_accel", "mdpd_set_state_accel",
+    "mdpd_get_accel", "mdpd_set_state_accel", "mdpd_eval_vjp_dev", "mdpd_window_forward",
+    "mdpd_window_vjp_dev",
 )
 
 
@@ -151,6 +152,9 @@ def lib(build_if_stale: bool = True):
     L.mdpd_density_vjp_dev.argtypes = [P, P, P]
     L.mdpd_get_accel.argtypes = [P, P]
     L.mdpd_set_state_accel.argtypes = [P, P, P, P]
+    L.mdpd_eval_vjp_dev.argtypes = [P, P, P, P, P, P, P]
+    L.mdpd_window_forward.argtypes = [P, i32]
+    L.mdpd_window_vjp_dev.argtypes = [P, P, P, P, P, P, P, P]
     L.mdpd_destroy.argtypes = [P]
     L.mdpd_destroy.restype = None
     L.mdpd_last_error.argtypes = [P]
@@ -409,6 +413,26 @@ def mdpd_force_vjp_dev(h, abar_t, xbar_t=None, ubar_t=None, theta_bar_t=None):
     abar/xbar/ubar (n, 3) float64, theta_bar (3, 8, 8) float64)."""
     _check(lib().mdpd_force_vjp_dev(h, _tptr(abar_t), _tptr(xbar_t), _tptr(ubar_t),
                                     _tptr(theta_bar_t)), h)
+
+
+def mdpd_eval_vjp_dev(h, abar_t=None, cvir_t=None, rhobar_t=None, xbar_t=None, ubar_t=None,
+                      theta_bar_t=None):
+    """VJP of one evaluation (accelerations, virial, densities) at the current
+    state; device tensors: abar/xbar/ubar (n, 3), cvir (nrep, 6), rhobar (n,),
+    theta_bar (nrep, 3, 8, 8) (or (3, 8, 8) for a single system), float64."""
+    _check(lib().mdpd_eval_vjp_dev(h, _tptr(abar_t), _tptr(cvir_t), _tptr(rhobar_t),
+                                   _tptr(xbar_t), _tptr(ubar_t), _tptr(theta_bar_t)), h)
+
+
+def mdpd_window_forward(h, nsteps: int):
+    _check(lib().mdpd_window_forward(h, int(nsteps)), h)
+
+
+def mdpd_window_vjp_dev(h, xbar_t=None, vbar_t=None, cvir_t=None, rhobar_t=None, x0bar_t=None,
+                        v0bar_t=None, theta_bar_t=None):
+    _check(lib().mdpd_window_vjp_dev(h, _tptr(xbar_t), _tptr(vbar_t), _tptr(cvir_t),
+                                     _tptr(rhobar_t), _tptr(x0bar_t), _tptr(v0bar_t),
+                                     _tptr(theta_bar_t)), h)
 
 
 class Tuned(tuple):
