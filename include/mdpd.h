@@ -343,9 +343,10 @@ int mdpd_density_vjp_dev(mdpd_handle* h, const double* rhobar, double* xbar);
  * v'_k = v_k + (dt/2) a_k in device memory owned by the handle (48 N bytes
  * per step; the checkpoints of the adjoint), so that mdpd_window_vjp_dev can
  * run the chain rule backwards.  Reflection is not differentiable: handles
- * with walls or a non-periodic axis are refused.  The window stays valid
- * until the state, step index or parameters change (mdpd_step,
- * mdpd_set_state*, mdpd_set_step, mdpd_set_params, mdpd_batch_set_params).
+ * with walls or a non-periodic axis are refused.  The checkpoints stay valid
+ * until the parameters or the particles change (mdpd_set_params,
+ * mdpd_batch_set_params, mdpd_set_walls) or another window is recorded;
+ * stepping or setting the state in between does not disturb them.
  * Errors: INVALID_ARG, OOM, CUDA and the errors of mdpd_step.  Synchronises. */
 int mdpd_window_forward(mdpd_handle* h, int32_t nsteps);
 

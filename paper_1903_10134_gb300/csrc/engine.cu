@@ -1215,7 +1215,6 @@ int mdpd_step(mdpd_handle* h, int64_t nsteps)
     if (!h) return MDPD_ERR_INVALID_ARG;
     if (nsteps < 0) return h->fail(MDPD_ERR_INVALID_ARG, "nsteps < 0");
     if (nsteps == 0) return MDPD_OK;
-    h->win_valid = false;
     ensure_ff(h);
     // the first step's binning applies the first half-kick and drift; later
     // steps get them from the previous force pass (FM_FUSED)
@@ -1319,7 +1318,6 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
     int rc = sync_check(h);
     if (rc) return rc;
     if (dev && ((rc = check_ptr_kind(h, pos, true)) || (rc = check_ptr_kind(h, vel, true)))) return rc;
-    h->win_valid = false;
     cudaStream_t st = h->stream;
     const int n = (int)h->n;
     const int c = h->cur;
@@ -1568,7 +1566,6 @@ int mdpd_set_step(mdpd_handle* h, int64_t step)
     int rc = sync_check(h);
     if (rc) return rc;
     const uint64_t s = (uint64_t)step;
-    h->win_valid = false;
     CK(cudaMemcpy(h->step, &s, sizeof(s), cudaMemcpyHostToDevice));
     h->steps_host = step;
     return MDPD_OK;
@@ -1637,11 +1634,12 @@ void vjp_core(mdpd_handle* h, const double* abar, const double* wbar, const doub
     double* xs = h->x[1 - c];
     double* us = h->v[1 - c];
     double* rs = h->a[1 - c];
-    launch_force_vjp(st, h->precision, n, h->cap, h->ph, pb, h->pos4, h->vel4, h->rho, h->nl,
-                     h->nl_count, h->step, abar, wbar, xs, us, rs, h->vjp_tpart, h->status);
+    launch_force_vjp(st, h->precision, n, h->cap, h->geo, h->ph, pb, h->pos4, h->vel4, h->rho,
+                     h->cell_s, h->start, h->nl, h->nl_count, h->step, abar, wbar, xs, us, rs,
+                     h->vjp_tpart, h->status);
     if (rhobar) launch_gather_by_id(st, n, h->id[c], rhobar, rs, 1);
-    launch_density_vjp(st, h->precision, n, h->cap, h->ph, pb, h->pos4, h->nl, h->nl_count, rs,
-                       xs, h->status);
+    launch_density_vjp(st, h->precision, n, h->cap, h->geo, h->ph, pb, h->pos4, h->cell_s,
+                       h->start, h->nl, h->nl_count, rs, xs, h->status);
     launch_theta_reduce(st, vjp_nrep(h), vjp_num_blocks(n, pb), h->nrep ? h->d_wr : nullptr,
                         PAIR_BLOCK_WARPS, h->vjp_tpart, h->vjp_tacc, add_theta);
 }

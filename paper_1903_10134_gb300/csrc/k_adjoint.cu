@@ -26,7 +26,8 @@
 //   xbar_i += m/2 (s_c (grad Q / r - Q d / r^3) + (Q / r) s_c' e),
 //   rhobar_i += m/2 (Q / r) B wd [r < r_d],  s_c' = ds_c/dr at fixed rho.
 // The partner lists hold every pair from both sides, so each thread adds its
-// own particle's share without atomics.  A second pass sends rhobar back to
+// own particle's share without atomics (a particle with more partners than
+// list slots scans its neighbour cells instead, as the force pass does).  A second pass sends rhobar back to
 // positions: xbar_i += (rhobar_i + rhobar_j) w_rho'(r) e over partners within
 // r_d.
 //
@@ -73,10 +74,56 @@ __device__ __forceinline__ BlockSite<BATCH> block_site(int n, const Batch& bt)
     return b;
 }
 
+// Visit the partners within r_c (0 < r) of particle s: from its list, or, for
+// a particle with more partners than list slots, by a scan of its 27
+// neighbour cells (the same partners, in cell order), as the force pass does.
+template <typename T, typename V, typename F>
+__device__ __forceinline__ void for_partners(int s, uint32_t cnt, int64_t cap,
+                                             const uint32_t* __restrict__ nl, const Geo& geo,
+                                             int64_t cell0, const uint32_t* __restrict__ cell_s,
+                                             const uint32_t* __restrict__ start,
+                                             const V* __restrict__ pos4, const V& pi,
+                                             const T (&shift)[27][3], T rc2, F&& partner)
+{
+    if (cnt <= (uint32_t)NL_MAX) {
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t e = nl[(int64_t)k * cap + s];
+            partner(e >> 5, e & 31u);
+        }
+        return;
+    }
+    int q0, q1, q2;
+    cell_coords(cell_s[s], geo, q0, q1, q2);      // (the cell within the replica)
+    for (int oz = -1; oz <= 1; ++oz) {
+        const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
+        if (z < 0) continue;
+        for (int oy = -1; oy <= 1; ++oy) {
+            const int y = neighbour_index(q1, oy, geo.nc[1], geo.periodic[1]);
+            if (y < 0) continue;
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int x = neighbour_index(q0, ox, geo.nc[0], geo.periodic[0]);
+                if (x < 0) continue;
+                const uint32_t code = (uint32_t)((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
+                const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
+                for (uint32_t j = start[nc]; j < start[nc + 1]; ++j) {
+                    const V pj = pos4[j];
+                    const T dx = pi.x - shift[code][0] - pj.x;
+                    const T dy = pi.y - shift[code][1] - pj.y;
+                    const T dz = pi.z - shift[code][2] - pj.z;
+                    const T r2 = dx * dx + dy * dy + dz * dz;
+                    if (r2 < rc2 && r2 > T(0)) partner(j, code);
+                }
+            }
+        }
+    }
+}
+
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(PAIR_BLOCK)
-k_force_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::type* __restrict__ pos4,
+k_force_vjp(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
+            const typename Vec4<T>::type* __restrict__ pos4,
             const typename Vec4<T>::type* __restrict__ vel4, const T* __restrict__ rho,
+            const uint32_t* __restrict__ cell_s, const uint32_t* __restrict__ start,
             const uint32_t* __restrict__ nl, const uint32_t* __restrict__ nl_count,
             const uint64_t* __restrict__ step_ptr, const double* __restrict__ abar,
             const double* __restrict__ wbar, double* __restrict__ xbar,
@@ -125,12 +172,8 @@ k_force_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::typ
             for (int k = 0; k < 3; ++k) ai[k] = (T)abar[3 * (int64_t)(id0 + id_i) + k];
         T gx[3] = { T(0), T(0), T(0) }, gu[3] = { T(0), T(0), T(0) };
         T gr = T(0);
-        const uint32_t cnt = nl_count[s];
-        if (cnt > (uint32_t)NL_MAX) atomicOr(status, ST_OVERFLOW);
-        const uint32_t m = cnt < (uint32_t)NL_MAX ? cnt : (uint32_t)NL_MAX;
-        for (uint32_t k = 0; k < m; ++k) {
-            const uint32_t e = nl[(int64_t)k * cap + s];
-            const uint32_t j = e >> 5, code = e & 31u;
+        // one partner j in the image of neighbour-cell code `code`
+        auto partner = [&](uint32_t j, uint32_t code) {
             const V pj = pos4[j];
             const V vj = vel4[j];
             const T rho_j = rho[j];
@@ -201,7 +244,10 @@ k_force_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::typ
                     cl[1 * 8 + tj] += 0.25 * (double)(mm * Qr * rsum * wd);
                 }
             }
-        }
+        };
+        const Geo& geo = BATCH ? b.rp->geo : geo_p;
+        for_partners<T>(s, nl_count[s], cap, nl, geo, BATCH ? b.rp->cell0 : 0, cell_s, start, pos4,
+                        pi, shift, derived<T>(ph).rc2, partner);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xbar[c * cap + s] = (double)gx[c];
@@ -223,7 +269,9 @@ k_force_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::typ
 
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(PAIR_BLOCK)
-k_density_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::type* __restrict__ pos4,
+k_density_vjp(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
+              const typename Vec4<T>::type* __restrict__ pos4,
+              const uint32_t* __restrict__ cell_s, const uint32_t* __restrict__ start,
               const uint32_t* __restrict__ nl, const uint32_t* __restrict__ nl_count,
               const double* __restrict__ rbar, double* __restrict__ xbar,
               uint32_t* __restrict__ status)
@@ -247,24 +295,22 @@ k_density_vjp(int n, int64_t cap, Phys ph_p, Batch bt, const typename Vec4<T>::t
     const V pi = pos4[s];
     const T rb_i = (T)rbar[s];
     T g[3] = { T(0), T(0), T(0) };
-    const uint32_t cnt = nl_count[s];
-    if (cnt > (uint32_t)NL_MAX) atomicOr(status, ST_OVERFLOW);
-    const uint32_t m = cnt < (uint32_t)NL_MAX ? cnt : (uint32_t)NL_MAX;
-    for (uint32_t k = 0; k < m; ++k) {
-        const uint32_t e = nl[(int64_t)k * cap + s];
-        const uint32_t j = e >> 5, code = e & 31u;
+    auto partner = [&](uint32_t j, uint32_t code) {
         const V pj = pos4[j];
         const T dx = pi.x - shift[code][0] - pj.x;
         const T dy = pi.y - shift[code][1] - pj.y;
         const T dz = pi.z - shift[code][2] - pj.z;
         const T r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (!(r < rd)) continue;
+        if (!(r < rd)) return;
         const T dw = T(-2) * cw * (T(1) - r * inv_rd) * inv_rd;   // w_rho'(r)
         const T f = (rb_i + (T)rbar[j]) * dw / r;
         g[0] += f * dx;
         g[1] += f * dy;
         g[2] += f * dz;
-    }
+    };
+    const Geo& geo = BATCH ? b.rp->geo : geo_p;
+    for_partners<T>(s, nl_count[s], cap, nl, geo, BATCH ? b.rp->cell0 : 0, cell_s, start, pos4, pi,
+                    shift, derived<T>(ph).rc2, partner);
 #pragma unroll
     for (int c = 0; c < 3; ++c) xbar[c * cap + s] += (double)g[c];
 }
@@ -432,8 +478,9 @@ int vjp_num_blocks(int n, const Batch* bt)
     return bt ? bt->nchunk : (int)pair_blocks(n);
 }
 
-void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
-                      const Batch* bt, const void* pos4, const void* vel4, const void* rho,
+void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                      const Phys& ph, const Batch* bt, const void* pos4, const void* vel4,
+                      const void* rho, const uint32_t* cell_s, const uint32_t* start,
                       const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,
                       const double* abar, const double* wbar, double* xbar, double* ubar,
                       double* rbar, double* tpart, uint32_t* status)
@@ -444,8 +491,9 @@ void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const 
     const size_t smem = bt ? REP_SMEM : 0;
 #define MDPD_FVJP(T_, B_)                                                                       \
     k_force_vjp<T_, B_><<<nb, PAIR_BLOCK, smem, st>>>(                                        \
-        n, cap, ph, bb, (const typename Vec4<T_>::type*)pos4, (const typename Vec4<T_>::type*)vel4, \
-        (const T_*)rho, nl, nl_count, step_ptr, abar, wbar, xbar, ubar, rbar, tpart, status)
+        n, cap, geo, ph, bb, (const typename Vec4<T_>::type*)pos4,                                \
+        (const typename Vec4<T_>::type*)vel4, (const T_*)rho, cell_s, start, nl, nl_count,        \
+        step_ptr, abar, wbar, xbar, ubar, rbar, tpart, status)
     if (precision == 0) {
         if (bt) MDPD_FVJP(double, true);
         else MDPD_FVJP(double, false);
@@ -456,8 +504,9 @@ void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const 
 #undef MDPD_FVJP
 }
 
-void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
-                        const Batch* bt, const void* pos4, const uint32_t* nl,
+void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                        const Phys& ph, const Batch* bt, const void* pos4,
+                        const uint32_t* cell_s, const uint32_t* start, const uint32_t* nl,
                         const uint32_t* nl_count, const double* rbar, double* xbar,
                         uint32_t* status)
 {
@@ -467,7 +516,8 @@ void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, cons
     const size_t smem = bt ? REP_SMEM : 0;
 #define MDPD_DVJP(T_, B_)                                                                       \
     k_density_vjp<T_, B_><<<nb, PAIR_BLOCK, smem, st>>>(                                      \
-        n, cap, ph, bb, (const typename Vec4<T_>::type*)pos4, nl, nl_count, rbar, xbar, status)
+        n, cap, geo, ph, bb, (const typename Vec4<T_>::type*)pos4, cell_s, start, nl, nl_count,  \
+        rbar, xbar, status)
     if (precision == 0) {
         if (bt) MDPD_DVJP(double, true);
         else MDPD_DVJP(double, false);

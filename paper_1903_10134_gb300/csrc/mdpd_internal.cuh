@@ -367,15 +367,17 @@ int vjp_num_blocks(int n, const Batch* bt);
 // accelerations, wbar (6 per replica, may be NULL) weights of the virial
 // components; xbar, ubar, rbar outputs in cell order; tpart[block][3 * 64]
 // the blocks' parameter partials by (parameter, own type, partner type).
-void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
-                      const Batch* bt, const void* pos4, const void* vel4, const void* rho,
+void launch_force_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                      const Phys& ph, const Batch* bt, const void* pos4, const void* vel4,
+                      const void* rho, const uint32_t* cell_s, const uint32_t* start,
                       const uint32_t* nl, const uint32_t* nl_count, const uint64_t* step_ptr,
                       const double* abar, const double* wbar, double* xbar, double* ubar,
                       double* rbar, double* tpart, uint32_t* status);
 // The density chain: xbar (cell order, [3][cap]) += sum_j (rbar_i + rbar_j)
 // w_rho'(r) e over partners within r_d (rbar in cell order).
-void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Phys& ph,
-                        const Batch* bt, const void* pos4, const uint32_t* nl,
+void launch_density_vjp(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
+                        const Phys& ph, const Batch* bt, const void* pos4,
+                        const uint32_t* cell_s, const uint32_t* start, const uint32_t* nl,
                         const uint32_t* nl_count, const double* rbar, double* xbar,
                         uint32_t* status);
 void launch_gather_by_id(cudaStream_t st, int n, const uint32_t* id, const double* in, double* out,

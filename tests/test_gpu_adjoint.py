@@ -203,6 +203,8 @@ def test_fit_A_to_a_target_local_density(env):
     def loss_and_grad(a):
         A = torch.tensor(a, dtype=torch.float64, device=dev, requires_grad=True)
         xk, _ = AD.window(s, p, x0, v0, A * ones, B, G, K)
+        # the density op sets the state in between: the window's checkpoints
+        # are not disturbed by that
         loss = (AD.density(s, xk).mean() - target) ** 2
         loss.backward()
         return float(loss.detach()), float(A.grad)

@@ -28,12 +28,14 @@ def _rel(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-30)
 
 
-def _uneven_replicas(nrep, seed, n_range=(150, 900), ntypes=2, frozen=()):
+def _uneven_replicas(nrep, seed, ntypes=2, frozen=()):
+    """Replicas of uneven box and size at number density 5 to 7 (the
+    liquid's), two types with distinct tables."""
     rng = np.random.default_rng(seed)
     ws = []
     for r in range(nrep):
-        n = int(rng.integers(*n_range))
-        L = (float(rng.uniform(3.2, 4.6)), float(rng.uniform(3.2, 4.6)), float(rng.uniform(3.2, 4.6)))
+        L = (float(rng.uniform(3.2, 5.5)), float(rng.uniform(3.2, 5.5)), float(rng.uniform(3.2, 5.5)))
+        n = int(rng.uniform(5.0, 7.0) * L[0] * L[1] * L[2])
         w = I.tiny(n, L, seed * 100 + r, ntypes=ntypes, frozen_types=frozen)
         ws.append(w)
     return ws
@@ -155,22 +157,33 @@ def test_batch_window_50_steps_matches_oracle_and_finite_differences(env):
                             observables=True)
             return float(loss_of(*out))
 
+    log = []
+
     def fd(f, eps):
         d1 = (f(eps) - f(-eps)) / (2 * eps)
         d2 = (f(2 * eps) - f(-2 * eps)) / (4 * eps)
+        log.append((round(d1, 6), round(d2, 6)))
         return d1 if abs(d1 - d2) <= 1e-5 * max(1.0, abs(d1)) else None
 
+    # directions supported on one replica (the others' terms cancel exactly
+    # in the differences, so small steps stay far above round-off); a
+    # direction whose interval moves a pair across r_c or r_d within the 50
+    # steps (the forces have a kink there) is detected by two step sizes and
+    # skipped
     checked = 0
-    for _ in range(2):
-        dx = torch.tensor(rng.normal(size=xs.shape), device=dev)
-        d = fd(lambda e: fwd(x0.detach() + e * dx, v0.detach()), 1e-7)
+    for r in (3, 17, 40, 58):
+        a0, a1 = b.offsets[r], b.offsets[r + 1]
+        dx = torch.zeros_like(x0)
+        dx[a0:a1] = torch.tensor(rng.normal(size=(a1 - a0, 3)), device=dev)
+        d = fd(lambda e: fwd(x0.detach() + e * dx, v0.detach()), 1e-8)
         if d is not None:
-            assert abs(d - float((x0.grad * dx).sum())) <= 1e-3 * max(1.0, abs(d))
+            assert abs(d - float((x0.grad * dx).sum())) <= 1e-3 * max(1.0, abs(d)), r
             checked += 1
-        dv = torch.tensor(rng.normal(size=xs.shape), device=dev)
-        d = fd(lambda e: fwd(x0.detach(), v0.detach() + e * dv), 1e-7)
+        dv = torch.zeros_like(v0)
+        dv[a0:a1] = torch.tensor(rng.normal(size=(a1 - a0, 3)), device=dev)
+        d = fd(lambda e: fwd(x0.detach(), v0.detach() + e * dv), 1e-8)
         if d is not None:
-            assert abs(d - float((v0.grad * dv).sum())) <= 1e-3 * max(1.0, abs(d))
+            assert abs(d - float((v0.grad * dv).sum())) <= 1e-3 * max(1.0, abs(d)), r
             checked += 1
     for r in (0, 31, 63):
         for name, T in (("A", A), ("B", B)):
@@ -181,36 +194,43 @@ def test_batch_window_50_steps_matches_oracle_and_finite_differences(env):
                 if name == "A":
                     return fwd(x0.detach(), v0.detach(), AA=A.detach() + e * E)
                 return fwd(x0.detach(), v0.detach(), BB=B.detach() + e * E)
-            d = fd(f, 1e-6)
+            d = fd(f, 1e-7)
             if d is not None:
                 assert abs(d - float(T.grad[r, 0, 0])) <= 1e-3 * max(1.0, abs(d)), (r, name)
                 checked += 1
-    assert checked >= 6
+    assert checked >= 8, log
 
 
 def test_fit_A_B_to_target_density_and_surface_tension(env):
-    """Batched calibration: 16 slab replicas of uneven size start from
-    (A, B) drawn in [-50, -30] x [15, 35]; each replica's target is the mean
-    local density and the surface tension (L_x / 2)(P_xx - (P_yy + P_zz)/2)
-    (Sec. 4.1; two interfaces) after a 50-step window from the same state made
-    with (A, B) = (-40, 25).  Gauss-Newton on the two residuals, with both
-    rows of each replica's Jacobian from the batched window gradient, recovers
-    (-40, 25) in every replica."""
+    """Batched calibration of (A, B) to a target density and surface tension.
+
+    128 slab replicas of uneven size (1,000 to 2,500 particles) form four
+    ensembles of 32; the replicas of an ensemble share one (A, B), and the
+    four ensembles start at the corners of [-50, -30] x [15, 35].  An
+    ensemble's observables are its replicas' mean local density (Sec. 2.1)
+    and mean surface tension (L_x / 2)(P_xx - (P_yy + P_zz)/2) (Sec. 4.1, two
+    interfaces) after a 20-step window; the targets are the same observables
+    made with (A, B) = (-40, 25) from the same states and random streams.
+    Levenberg-Marquardt, with both rows of each ensemble's 2 x 2 Jacobian
+    from batched window gradients (one launch per kernel for all 128
+    replicas), recovers (-40, 25) in every ensemble.  (One small slab's
+    instantaneous surface tension is too noisy to fit on its own, and over
+    much longer windows the trajectory's chaos makes the gradient of a single
+    realisation rough: the ensemble mean over a short window is smooth.)"""
     torch, M, AD = env
     dev = "cuda"
-    nrep = 16
+    nrep, ngrp = 128, 4
     ws = _slab_batch(nrep, 33, n_range=(1000, 2500))
-    rng = np.random.default_rng(34)
     ps = []
     for w in ws:
         p = w.params.copy()
         p.A[:] = -40.0
         p.B[:] = 25.0
         ps.append(p)
-    b = M.Batch([p for p in ps], [w.n for w in ws], np.concatenate([w.pos for w in ws]),
+    b = M.Batch(ps, [w.n for w in ws], np.concatenate([w.pos for w in ws]),
                 np.concatenate([w.vel for w in ws]), np.concatenate([w.type for w in ws]),
                 [w.seed for w in ws])
-    b.step(300)                            # a slab at (-40, 25)
+    b.step(300)                            # slabs at (-40, 25)
     b.sync()
     xs, vs, _, _ = b.state()
     x0 = torch.tensor(xs, device=dev)
@@ -222,9 +242,11 @@ def test_fit_A_B_to_target_density_and_surface_tension(env):
     seg = torch.repeat_interleave(torch.arange(nrep, device=dev),
                                   torch.tensor(b.n_list, device=dev))
     counts = torch.tensor(b.n_list, dtype=torch.float64, device=dev)
-    K = 50
+    grp = torch.arange(nrep, device=dev) % ngrp
+    K = 20
 
-    def observables(theta):
+    def observables(theta_g):
+        theta = theta_g[grp]
         A = theta[:, 0, None, None] * ones
         B = theta[:, 1, None, None] * ones
         xk, vk, rho, W = AD.window(b, ps, x0, v0, A, B, G, K, step0=300, observables=True)
@@ -232,26 +254,45 @@ def test_fit_A_B_to_target_density_and_surface_tension(env):
         dens = torch.zeros(nrep, dtype=torch.float64, device=dev).index_add_(0, seg, rho) / counts
         P = (kin + W[:, :3]) / vol[:, None]
         gam = 0.5 * lx * (P[:, 0] - 0.5 * (P[:, 1] + P[:, 2]))
-        return dens, gam
+        per = float(nrep // ngrp)
+        dg = torch.zeros(ngrp, dtype=torch.float64, device=dev).index_add_(0, grp, dens) / per
+        gg = torch.zeros(ngrp, dtype=torch.float64, device=dev).index_add_(0, grp, gam) / per
+        return dg, gg
 
-    star = torch.tensor([[-40.0, 25.0]] * nrep, dtype=torch.float64, device=dev)
+    star = torch.tensor([[-40.0, 25.0]] * ngrp, dtype=torch.float64, device=dev)
     with torch.no_grad():
         d_t, g_t = observables(star)
-    theta = torch.tensor(np.stack([rng.uniform(-50, -30, nrep), rng.uniform(15, 35, nrep)], 1),
-                         dtype=torch.float64, device=dev)
-    for it in range(12):
-        th = theta.clone().requires_grad_(True)
+
+    def residuals(th):
         dens, gam = observables(th)
-        r1 = (dens - d_t) / d_t
-        r2 = (gam - g_t) / g_t.abs()
-        J1 = torch.autograd.grad(r1.sum(), th, retain_graph=True)[0]      # (nrep, 2)
-        J2 = torch.autograd.grad(r2.sum(), th)[0]
-        J = torch.stack([J1, J2], 1)                                      # (nrep, 2, 2)
-        res = torch.stack([r1, r2], 1).detach()
-        step = torch.linalg.solve(J, -res.unsqueeze(-1)).squeeze(-1)
-        step = step.clamp(-6.0, 6.0)                                       # a trust region
-        theta = theta + step
-        if float(step.abs().max()) < 1e-6:
+        return torch.stack([(dens - d_t) / d_t, (gam - g_t) / 10.0], 1)
+
+    # Levenberg-Marquardt per ensemble: a trial step is kept where it lowers
+    # that ensemble's residual, else its damping grows
+    theta = torch.tensor([[-46.0, 19.0], [-34.0, 31.0], [-46.0, 31.0], [-34.0, 19.0]],
+                         dtype=torch.float64, device=dev)
+    lam = torch.full((ngrp,), 1e-2, dtype=torch.float64, device=dev)
+    hist = []
+    for it in range(60):
+        th = theta.clone().requires_grad_(True)
+        res = residuals(th)
+        J1 = torch.autograd.grad(res[:, 0].sum(), th, retain_graph=True)[0]
+        J2 = torch.autograd.grad(res[:, 1].sum(), th)[0]
+        J = torch.stack([J1, J2], 1)                                  # (ngrp, 2, 2)
+        res = res.detach()
+        f0 = (res ** 2).sum(1)
+        hist.append(float(f0.max()))
+        if hist[-1] < 1e-20:
             break
+        JtJ = J.transpose(1, 2) @ J
+        D = torch.diag_embed(torch.diagonal(JtJ, dim1=1, dim2=2))
+        g = J.transpose(1, 2) @ res.unsqueeze(-1)
+        step = torch.linalg.solve(JtJ + lam[:, None, None] * D, -g).squeeze(-1)
+        trial = theta + step.clamp(-2.0, 2.0)                        # a trust region
+        with torch.no_grad():
+            f1 = (residuals(trial) ** 2).sum(1)
+        ok = f1 < f0
+        theta = torch.where(ok[:, None], trial, theta)
+        lam = torch.where(ok, lam / 3.0, lam * 4.0).clamp(1e-12, 1e12)
     err = (theta - star).abs().cpu().numpy()
-    assert err[:, 0].max() < 0.4 and err[:, 1].max() < 0.25, (theta.cpu().numpy(), it)
+    assert err[:, 0].max() < 0.4 and err[:, 1].max() < 0.25, (theta.cpu().numpy(), it, hist)
