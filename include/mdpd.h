@@ -47,7 +47,9 @@ enum {
     MDPD_ERR_OUT_OF_BOX = -5,    /* a particle left a non-periodic box       */
     MDPD_ERR_TILE_OVERFLOW = -6, /* a cell held more particles than a kernel
                                     tile can stage                           */
-    MDPD_ERR_TIMEOUT = -7        /* a bounded device wait gave up            */
+    MDPD_ERR_TIMEOUT = -7,       /* a bounded device wait gave up            */
+    MDPD_ERR_BOUNDS = -8         /* an index check of the debug build failed
+                                    (libmdpd_gb300_debug.so only)            */
 };
 
 /* System parameters (Sec. 2.1, Eq. 1).  Pair tables are indexed [type_i][type_j]

@@ -3,6 +3,12 @@
 Each translation unit under ``csrc/`` is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and the objects are
 linked into one shared library next to this file.  No CPU fallback is built.
+
+``build(debug=True)`` compiles the same sources with ``-DMDPD_DEBUG`` into
+``libmdpd_gb300_debug.so``: every computed index of the pair kernels is checked
+against its array, and a failed check sets a bit of the handle's status word
+(reported as MDPD_ERR_BOUNDS) and skips the access instead of trapping.  The
+binding loads it when the environment variable MDPD_DEBUG is 1.
 """
 from __future__ import annotations
 
@@ -18,6 +24,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmdpd_gb300.so")
+BUILD_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libmdpd_gb300_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -41,23 +49,27 @@ def _deps() -> list[str]:
     return files + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile (if stale) and return the path of the library."""
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          debug: bool = False) -> str:
+    """Compile (if stale) and return the path of the library (the index-checking
+    debug variant with debug=True)."""
+    lib = LIB_DEBUG if debug else LIB
+    bdir = BUILD_DEBUG if debug else BUILD
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     nv = nvcc()
-    flags = FLAGS + list(extra_flags or [])
+    flags = FLAGS + (["-DMDPD_DEBUG"] if debug else []) + list(extra_flags or [])
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [nv] + ARCH + flags + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -69,16 +81,17 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nv] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force=True, verbose=v or bool(extra), extra_flags=extra))
+    print(build(force=True, verbose=v or bool(extra), extra_flags=extra,
+                debug="--debug" in sys.argv))

@@ -395,10 +395,12 @@ void setup_geo_phys(mdpd_handle* h)
     h->ph = Phys{};
     make_geo_phys(h->p, h->seed, h->geo, h->ph);
     h->ph.list_all = list_all;
+    h->ph.dbg_status = h->status;
 }
 
 int status_to_code(uint32_t st)
 {
+    if (st & ST_BOUNDS) return MDPD_ERR_BOUNDS;      // (a failed check can cause the rest)
     if (st & ST_NONFINITE) return MDPD_ERR_NONFINITE;
     if (st & ST_OUT_OF_BOX) return MDPD_ERR_OUT_OF_BOX;
     if (st & ST_OVERFLOW) return MDPD_ERR_TILE_OVERFLOW;
@@ -422,6 +424,7 @@ int sync_check(mdpd_handle* h)
         const char* what = code == MDPD_ERR_NONFINITE     ? "non-finite position, velocity or force"
                            : code == MDPD_ERR_OUT_OF_BOX   ? "a particle left a non-periodic box"
                            : code == MDPD_ERR_TILE_OVERFLOW ? "cell tile overflow"
+                           : code == MDPD_ERR_BOUNDS ? "an index check of the debug build failed"
                                                             : "device wait timed out";
         return h->fail(code, what);
     }
@@ -728,6 +731,8 @@ int check_ptr_kind(mdpd_handle* h, const void* p, bool want_device)
 // (particle i of replica r must have a type below ntypes[r]; replica r holds
 // the ids [bounds[r], bounds[r + 1])), allocations, upload, loading and the
 // first force evaluation.  Owns h: destroys it on failure.
+int upload_reps(mdpd_handle* h);
+
 int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int32_t* type,
                 void* stream, bool device_inputs, const std::vector<int64_t>& bounds,
                 const std::vector<int>& ntypes, mdpd_handle** out)
@@ -792,6 +797,11 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
         (rc = dalloc(h, &h->red_ticket, sizeof(unsigned))) ||
         (rc = dalloc(h, &h->obs, (2 * MDPD_NUM_OBS + 2) * sizeof(double))))
         return bail(rc);
+    h->ph.dbg_status = h->status;
+    if (h->nrep) {
+        for (auto& R : h->reps) R.ph.dbg_status = h->status;
+        if ((rc = upload_reps(h))) return bail(rc);
+    }
     for (int k = 0; k < EV_PER_STEP; ++k)
         if (cudaEventCreate(&h->tev[k]) != cudaSuccess) {
             h->err = "cudaEventCreate failed";
@@ -1058,6 +1068,7 @@ int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params)
         make_geo_phys(params[r], 0, g, R.ph);
         R.ph.key0 = k0;
         R.ph.key1 = k1;
+        R.ph.dbg_status = h->status;
         philox_round_keys(k0, k1, R.ph.rk);
         h->rep_p[r] = params[r];
     }

@@ -83,12 +83,14 @@ __device__ __forceinline__ void for_partners(int s, uint32_t cnt, int64_t cap,
                                              int64_t cell0, const uint32_t* __restrict__ cell_s,
                                              const uint32_t* __restrict__ start,
                                              const V* __restrict__ pos4, const V& pi,
-                                             const T (&shift)[27][3], T rc2, F&& partner)
+                                             const T (&shift)[27][3], T rc2,
+                                             uint32_t* __restrict__ dbg, F&& partner)
 {
     if (cnt <= (uint32_t)NL_MAX) {
         for (uint32_t k = 0; k < cnt; ++k) {
             const uint32_t e = nl[(int64_t)k * cap + s];
-            partner(e >> 5, e & 31u);
+            if (MDPD_DBG_OK((e >> 5) < (uint32_t)cap && (e & 31u) < 27u, dbg))
+                partner(e >> 5, e & 31u);
         }
         return;
     }
@@ -105,7 +107,10 @@ __device__ __forceinline__ void for_partners(int s, uint32_t cnt, int64_t cap,
                 if (x < 0) continue;
                 const uint32_t code = (uint32_t)((ox + 1) + 3 * (oy + 1) + 9 * (oz + 1));
                 const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
-                for (uint32_t j = start[nc]; j < start[nc + 1]; ++j) {
+                const uint32_t b = start[nc];
+                uint32_t e = start[nc + 1];
+                if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)cap, dbg)) e = b;
+                for (uint32_t j = b; j < e; ++j) {
                     const V pj = pos4[j];
                     const T dx = pi.x - shift[code][0] - pj.x;
                     const T dy = pi.y - shift[code][1] - pj.y;
@@ -247,7 +252,7 @@ k_force_vjp(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
         };
         const Geo& geo = BATCH ? b.rp->geo : geo_p;
         for_partners<T>(s, nl_count[s], cap, nl, geo, BATCH ? b.rp->cell0 : 0, cell_s, start, pos4,
-                        pi, shift, derived<T>(ph).rc2, partner);
+                        pi, shift, derived<T>(ph).rc2, ph.dbg_status, partner);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             xbar[c * cap + s] = (double)gx[c];
@@ -310,7 +315,7 @@ k_density_vjp(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     };
     const Geo& geo = BATCH ? b.rp->geo : geo_p;
     for_partners<T>(s, nl_count[s], cap, nl, geo, BATCH ? b.rp->cell0 : 0, cell_s, start, pos4, pi,
-                    shift, derived<T>(ph).rc2, partner);
+                    shift, derived<T>(ph).rc2, ph.dbg_status, partner);
 #pragma unroll
     for (int c = 0; c < 3; ++c) xbar[c * cap + s] += (double)g[c];
 }

@@ -136,6 +136,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 const uint32_t code = (uint32_t)image_code(ox, oy, oz);
                 const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
                 uint32_t b = start[nc], e = start[nc + 1];
+                if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)cap, ph.dbg_status)) e = b;
                 if (FS == 1 && !mobile) e = min(max(mend[nc], b), e);     // mobile slots
                 // the common path is one distance test: r_d <= r_c, so the
                 // density term and the list append sit inside the r < r_c
@@ -225,7 +226,8 @@ __device__ __forceinline__ void density_cell_warp(int64_t c, int64_t cell0, cons
         if (x >= 0 && y >= 0 && z >= 0) {
             const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
             cb = start[nc];
-            cn = start[nc + 1] - cb;
+            const uint32_t ce = start[nc + 1];
+            cn = MDPD_DBG_OK(cb <= ce && ce <= (uint32_t)cap, ph.dbg_status) ? ce - cb : 0u;
         }
     }
     uint32_t inc = cn;

@@ -127,13 +127,22 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
         const uint32_t cnt = nl_count[s];
         if (cnt <= (uint32_t)NL_MAX) {
             const uint32_t k0 = (uint32_t)sub;
-            uint32_t e0 = k0 < cnt ? nl[(int64_t)k0 * cap + s] : 0u;
-            uint32_t e1 = k0 + LPP < cnt ? nl[(int64_t)(k0 + LPP) * cap + s] : 0u;
+            // (debug build: an entry naming a slot beyond the arrays or a code
+            // beyond 26 is reported and replaced by entry 0, so the access
+            // stays inside the arrays; the result is then wrong and flagged)
+            auto entry = [&](uint32_t k) -> uint32_t {
+                if (k >= cnt) return 0u;
+                const uint32_t e = nl[(int64_t)k * cap + s];
+                return MDPD_DBG_OK((e >> 5) < (uint32_t)cap && (e & 31u) < 27u, ph.dbg_status)
+                           ? e : 0u;
+            };
+            uint32_t e0 = entry(k0);
+            uint32_t e1 = entry(k0 + LPP);
             V pj = pos4[e0 >> 5];
             V vj = vel4[e0 >> 5];
             T rj = rho[e0 >> 5];
             for (uint32_t k = k0; k < cnt; k += LPP) {
-                const uint32_t e2 = k + 2 * LPP < cnt ? nl[(int64_t)(k + 2 * LPP) * cap + s] : 0u;
+                const uint32_t e2 = entry(k + 2 * LPP);
                 const V pn = pos4[e1 >> 5];
                 const V vn = vel4[e1 >> 5];
                 const T rn = rho[e1 >> 5];
@@ -166,7 +175,9 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                         if (x < 0) continue;
                         const int code = image_code(ox, oy, oz);
                         const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
-                        const uint32_t b = start[nc], e = start[nc + 1];
+                        const uint32_t b = start[nc];
+                        uint32_t e = start[nc + 1];
+                        if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)cap, ph.dbg_status)) e = b;
                         for (uint32_t j = b; j < e; ++j) {
                             const V pj = pos4[j];
                             const V sh = shift[code];

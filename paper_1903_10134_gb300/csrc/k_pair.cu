@@ -53,7 +53,9 @@ k_density(int n, Geo geo, Phys ph, const typename Vec4<T>::type* __restrict__ po
                 }
                 const T sx = pi.x - (T)ox * derived<T>(ph).h[0];
                 const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
-                const uint32_t b = start[nc], e = start[nc + 1];
+                const uint32_t b = start[nc];
+                uint32_t e = start[nc + 1];
+                if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)n, ph.dbg_status)) e = b;
                 for (uint32_t j = b; j < e; ++j) {
                     if (j == (uint32_t)s) continue;
                     const auto pj = pos4[j];
@@ -120,7 +122,9 @@ k_force(int n, int64_t cap, Geo geo, Phys ph, MaskDev mk,
                         if (x < 0) continue;
                         const T sx = pi.x - (T)ox * derived<T>(ph).h[0];
                         const uint32_t nc = (uint32_t)(x + geo.nc[0] * (y + geo.nc[1] * z));
-                        const uint32_t b = start[nc], e = start[nc + 1];
+                        const uint32_t b = start[nc];
+                        uint32_t e = start[nc + 1];
+                        if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)n, ph.dbg_status)) e = b;
                         for (uint32_t j = b; j < e; ++j) {
                             const auto pj = pos4[j];
                             const T dx = sx - pj.x, dy = sy - pj.y, dz = sz - pj.z;

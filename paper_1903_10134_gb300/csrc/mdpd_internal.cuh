@@ -18,7 +18,18 @@ enum : uint32_t {
     ST_OUT_OF_BOX = 2u,
     ST_OVERFLOW = 4u,
     ST_TIMEOUT = 8u,
+    ST_BOUNDS = 16u,     // an index check of the debug build failed
 };
+
+// Index checks of the debug build (compiled with -DMDPD_DEBUG): a computed
+// index outside its array sets ST_BOUNDS in the status word and the access is
+// skipped (never a trap).  In the release build the check is the constant
+// true and costs nothing.
+#ifdef MDPD_DEBUG
+#define MDPD_DBG_OK(cond, status) ((cond) ? true : (atomicOr((status), ::mdpd::ST_BOUNDS), false))
+#else
+#define MDPD_DBG_OK(cond, status) true
+#endif
 
 // Cell lattice and box (edge h >= r_c on every axis; x fastest).
 struct Geo {
@@ -61,6 +72,7 @@ struct Phys {
     int prec32;                   // 1: FP32 pair arithmetic (kick increments formed in FP32)
     uint32_t fast_cell;           // bit k: axis k may take cell indices in FP32 (see k_bin_count)
     void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr
+    uint32_t* dbg_status;         // the handle's status word (index checks of the debug build)
     uint32_t key0, key1;          // Philox key = (seed_lo, seed_hi)
     uint32_t rk[10][2];           // its ten round keys (key + r * Weyl increments; set_keys)
     Derived<float> df;

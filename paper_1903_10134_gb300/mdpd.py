@@ -34,7 +34,7 @@ KCLASS = ("bin", "density", "force", "other")
 
 ERRORS = {
     -1: "INVALID_ARG", -2: "OOM", -3: "CUDA", -4: "NONFINITE",
-    -5: "OUT_OF_BOX", -6: "TILE_OVERFLOW", -7: "TIMEOUT",
+    -5: "OUT_OF_BOX", -6: "TILE_OVERFLOW", -7: "TIMEOUT", -8: "BOUNDS",
 }
 
 _lib = None
@@ -104,16 +104,24 @@ SYMBOLS = (
 )
 
 
+def debug_build() -> bool:
+    """Whether this process uses the index-checking debug build of the library
+    (environment variable MDPD_DEBUG=1)."""
+    return os.environ.get("MDPD_DEBUG", "0") == "1"
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_build() else _build.LIB
 
 
 def lib(build_if_stale: bool = True):
-    """Load the CUDA library (compiling it first if it is missing or stale)."""
+    """Load the CUDA library (compiling it first if it is missing or stale);
+    the debug build when MDPD_DEBUG=1."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build() if build_if_stale else _build.LIB
+    dbg = debug_build()
+    path = _build.build(debug=dbg) if build_if_stale else library_path()
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
     L = C.CDLL(path)

@@ -99,3 +99,15 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.mdpd_sync(None) == -1
     assert lib.mdpd_get_state(None, None, None, None, None) == -1
     lib.mdpd_destroy(None)
+
+
+def test_debug_library_builds_and_exports_every_declared_symbol():
+    """The index-checking build (-DMDPD_DEBUG, libmdpd_gb300_debug.so)
+    compiles for sm_103a and exports the same entry points."""
+    path = _build.build(debug=True)
+    assert path == _build.LIB_DEBUG and os.path.exists(path)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(mdpd_[a-z0-9_]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
