@@ -163,18 +163,32 @@ MDPD_HD double u32_to_f64(uint32_t q)
 
 #if defined(__CUDACC__)
 // The same with the hardware conversion for the rare inputs the integer
-// paths leave out.
+// paths leave out.  The fallback sits behind a branch that a warp takes only
+// when one of its active lanes needs it: written as a select, the hardware
+// conversion (an FP64-pipe instruction) ran on every call and kept that pipe
+// the busiest unit of the binning kernel.
+// (The hardware conversions sit in functions that are not inlined, so the
+// compiler cannot run them speculatively ahead of the branch.)
+static __device__ __noinline__ float hw_f64_to_f32(double x) { return __double2float_rn(x); }
+static __device__ __noinline__ double hw_f32_to_f64(float x) { return (double)x; }
+
 __device__ __forceinline__ float to_f32(double x)
 {
     bool ok;
-    const float f = f64_to_f32_rn(x, &ok);
-    return ok ? f : (float)x;
+    float f = f64_to_f32_rn(x, &ok);
+    if (__any_sync(__activemask(), !ok)) {
+        if (!ok) f = hw_f64_to_f32(x);
+    }
+    return f;
 }
 __device__ __forceinline__ double to_f64(float x)
 {
     bool ok;
-    const double d = f32_to_f64(x, &ok);
-    return ok ? d : (double)x;
+    double d = f32_to_f64(x, &ok);
+    if (__any_sync(__activemask(), !ok)) {
+        if (!ok) d = hw_f32_to_f64(x);
+    }
+    return d;
 }
 template <typename T>
 __device__ __forceinline__ T to_t(double x);

@@ -70,14 +70,22 @@ __global__ void k_bin_count(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, 
             q[k] = 0;
             continue;
         }
-        int c;
         const float fl = floorf(t);
-        if (((ph.fast_cell >> k) & 1u) && t - fl > 2e-3f && fl + 1.0f - t > 2e-3f) {
-            c = (int)fl;
-        } else {
-            c = (int)floor((xk - geo.lo[k]) * geo.inv_h[k]);
+        int c = (int)fl;
+        const bool exact = ((ph.fast_cell >> k) & 1u) && t - fl > 2e-3f && fl + 1.0f - t > 2e-3f;
+        // the FP64 index behind a branch that a warp takes only when one of
+        // its lanes needs it (if-converted, its four FP64 instructions ran
+        // for every particle and were most of this kernel's time)
+        if (__any_sync(__activemask(), !exact)) {
+            if (!exact) c = (int)floor_index_f64(xk, geo.lo[k], geo.inv_h[k], 0.0, 0);
         }
-        if (!geo.periodic[k] && (xk < geo.lo[k] || xk >= geo.hi[k])) st |= ST_OUT_OF_BOX;
+        // the face test on order-preserving integer keys of the FP64 bits
+        // (f64_key), under a uniform branch: as FP64 comparisons it cost
+        // most of this kernel's time (FP64 runs at 1/64 of the FP32 rate)
+        if (!geo.periodic[k]) {
+            const int64_t kx = f64_key(xk);
+            if (kx < geo.key_lo[k] || kx >= geo.key_hi[k]) st |= ST_OUT_OF_BOX;
+        }
         c = c < 0 ? 0 : (c >= geo.nc[k] ? geo.nc[k] - 1 : c);
         q[k] = c;
     }
@@ -319,10 +327,14 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
             off[k] = o;
         }
     }
-    if (!done) {            // FP64 pairs, or a coordinate outside the FP32 split's range
+    // FP64 pairs, or a coordinate outside the FP32 split's range (a
+    // warp-voted branch: FP64 instructions cost 64 FP32 issue slots)
+    if (__any_sync(__activemask(), !done)) {
+        if (!done) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
-            off[k] = to_t<T>(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
+            for (int k = 0; k < 3; ++k)
+                off[k] = to_t<T>(xv[k] - fma((double)q[k], geo.h[k], ph_g.dd.c0[k]));
+        }
     }
     pos4[s] = make4(off[0], off[1], off[2], pack_u32(T(0), (uint32_t)pt));
     // the random stream is keyed on ids within the replica

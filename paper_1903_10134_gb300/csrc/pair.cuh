@@ -100,6 +100,16 @@ __device__ __forceinline__ void pair_term(const PairConst<T>& c, const V4& prm, 
     W[5] += fv * dy * dz;
 }
 
+// floor((x - lo) * s) or floor((x - lo) / d) in FP64 (div: d used), the exact
+// cell or voxel index for the rare coordinates near a face.  Not inlined, so
+// that the compiler cannot execute its FP64 instructions speculatively for
+// every particle (FP64 runs at 1/64 of the FP32 rate on this part).
+static __device__ __noinline__ double floor_index_f64(double x, double lo, double s, double d, int div)
+{
+    const double t = __dsub_rn(x, lo);
+    return floor(div ? __ddiv_rn(t, d) : __dmul_rn(t, s));
+}
+
 // Drift by dt with velocity v, wrap periodic axes, and undo the drift with a
 // negated velocity if the new position is beyond a non-periodic face or in a
 // solid voxel.  Explicit round-to-nearest operations keep each product and
@@ -116,8 +126,12 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
         // (f64_key orders like the FP64 comparison, off the FP64 pipe)
         const int64_t kx = f64_key(xn[k]);
         if (geo.periodic[k]) {
-            if (kx >= geo.key_hi[k]) xn[k] = __dsub_rn(xn[k], geo.L[k]);
-            else if (kx < geo.key_lo[k]) xn[k] = __dadd_rn(xn[k], geo.L[k]);
+            // the rare wrap behind a warp-voted branch (FP64 adds)
+            const bool up = kx >= geo.key_hi[k], down = kx < geo.key_lo[k];
+            if (__any_sync(__activemask(), up || down)) {
+                if (up) xn[k] = __dsub_rn(xn[k], geo.L[k]);
+                else if (down) xn[k] = __dadd_rn(xn[k], geo.L[k]);
+            }
         } else if (kx < geo.key_lo[k] || kx >= geo.key_hi[k]) {
             blocked = true;
         }
@@ -129,22 +143,29 @@ __device__ __forceinline__ void drift_reflect(double (&x)[3], double (&v)[3], co
         for (int k = 0; k < 3; ++k) {
             // voxel index in FP32 when that cannot differ from the FP64 one
             // (mk.fast: FP32 error below 4e-4 voxels; the index is taken only
-            // 2e-3 voxels or more from a face), in FP64 otherwise
+            // 2e-3 voxels or more from a face), in FP64 otherwise; the FP64
+            // path sits behind a branch that a warp takes only when one of
+            // its lanes needs it (if-converted, it ran on the 1/64-rate FP64
+            // pipe for every particle)
+            bool done = false;
             if (mk.fast) {
                 const float t = (to_f32(xn[k]) - mk.origin_f[k]) * mk.inv_voxel_f;
                 const float fl = floorf(t);
                 if (t - fl > 2e-3f && fl + 1.0f - t > 2e-3f) {
                     if (!(fl >= 0.0f) || fl >= (float)mk.dim[k]) inside = false;
                     q[k] = inside ? (int64_t)fl : 0;
-                    continue;
+                    done = true;
                 }
             }
-            const double t = __dsub_rn(xn[k], mk.origin[k]);
-            // for a power-of-two voxel t * (1/voxel) is exactly t / voxel
-            const double f = floor(mk.inv_voxel_exact ? __dmul_rn(t, mk.inv_voxel)
-                                                      : __ddiv_rn(t, mk.voxel));
-            if (!(f >= 0.0) || f >= (double)mk.dim[k]) inside = false;
-            q[k] = inside ? (int64_t)f : 0;
+            if (__any_sync(__activemask(), !done)) {
+                if (!done) {
+                    // for a power-of-two voxel t * (1/voxel) is exactly t / voxel
+                    const double f = floor_index_f64(xn[k], mk.origin[k], mk.inv_voxel,
+                                                     mk.voxel, !mk.inv_voxel_exact);
+                    if (!(f >= 0.0) || f >= (double)mk.dim[k]) inside = false;
+                    q[k] = inside ? (int64_t)f : 0;
+                }
+            }
         }
         if (inside) {
             const int64_t idx = q[0] + (int64_t)mk.dim[0] * (q[1] + (int64_t)mk.dim[1] * q[2]);
