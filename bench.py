@@ -254,17 +254,17 @@ def candidate_tests(x, params, ncell, frozen=None) -> int:
     """Candidate tests of one density pass: every particle is tested against
     every particle of its 27 neighbour cells (itself included), so the count
     is sum over cells c of n_c times the particles in c's neighbourhood.  With
-    `frozen` (a per-particle flag; the split density pass), a frozen particle
-    is tested against the mobile particles of its neighbourhood only."""
+    `frozen` (a per-particle flag; the split density pass), only mobile
+    particles scan: a frozen particle's density is its constant frozen-frozen
+    part plus the terms its mobile neighbours scatter to it."""
     import numpy as np
     nc = np.array(ncell, dtype=np.int64)
     counts = _cell_counts(x, params, nc)
     neigh = _neighbourhood_sum(counts, params.periodic)
     if frozen is None or not np.any(frozen):
         return int((counts * neigh).sum())
-    cf = _cell_counts(x[frozen], params, nc)
-    cm = counts - cf
-    return int((cm * neigh).sum() + (cf * _neighbourhood_sum(cm, params.periodic)).sum())
+    cm = counts - _cell_counts(x[frozen], params, nc)
+    return int((cm * neigh).sum())
 
 
 OBS_NAMES = ("px", "py", "pz", "ke", "kT", "Wxx", "Wyy", "Wzz", "Wxy", "Wxz", "Wyz",
@@ -366,7 +366,7 @@ def precision_error(mdpd, s, w, workload):
 
 
 def oracle_error(mdpd, s, w, workload):
-    """Error of the FP32 path against the FP64 oracle (spec change 1) on
+    """Error of the FP32 path against the FP64 oracle on
     the bench's final state: the GPU evaluates densities, forces and
     observables once at its current state and step index (mdpd_forces), and
     the oracle evaluates the same state (positions, velocities, types, wall

@@ -69,10 +69,10 @@ struct mdpd_handle {
     // the scan's per-tile sums of the counts, formed by the count kernel; two
     // buffers of scan_num_blocks(ncell) words used by binning parity (cur)
     uint32_t* tile_sums = nullptr;
-    uint32_t* mend = nullptr;        // first frozen slot of each cell (see launch_rank_gather)
     // frozen-frozen part of each frozen particle's density, by id (constant
     // while the frozen particles and r_d stay; recomputed when ff_dirty)
     void* rho_ff = nullptr;
+    unsigned long long* facc = nullptr;  // cap fixed-point density sums of the frozen split
     bool ff_dirty = true;
     // misc
     uint32_t* status = nullptr;
@@ -224,6 +224,7 @@ void free_particles(mdpd_handle* h)
     dfree(h->nl_count);
     dfree(h->phi);
     dfree(h->rho_ff);
+    dfree(h->facc);
 }
 
 int alloc_particles(mdpd_handle* h, int64_t cap)
@@ -256,6 +257,11 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->nl_count, c * sizeof(uint32_t));
     if (!rc) rc = dalloc(h, &h->phi, c * tsz);
     if (!rc) rc = dalloc(h, &h->rho_ff, c * tsz);
+    if (!rc) rc = dalloc(h, &h->facc, c * sizeof(unsigned long long));
+    if (!rc && cudaMemset(h->facc, 0, c * sizeof(unsigned long long)) != cudaSuccess)
+        rc = h->fail(MDPD_ERR_CUDA, "cudaMemset of the frozen-split sums failed");
+    if (!rc && cudaDeviceSynchronize() != cudaSuccess)
+        rc = h->fail(MDPD_ERR_CUDA, "cudaDeviceSynchronize after allocation failed");
     if (!rc) h->cap = (int64_t)c;
     return rc;
 }
@@ -286,6 +292,7 @@ void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
     std::swap(a->nl_count, b->nl_count);
     std::swap(a->phi, b->phi);
     std::swap(a->rho_ff, b->rho_ff);
+    std::swap(a->facc, b->facc);
     std::swap(a->cap, b->cap);
 }
 
@@ -466,19 +473,21 @@ void enqueue_bin(mdpd_handle* h, bool gather_a, bool kick = false)
     if (h->nrep)
         launch_rank_gather_batch(st, h->precision, h->cap, h->cellof, h->start, h->key, h->src,
                                  master(h, h->cur), master(h, 1 - h->cur), gather_a, h->batch(),
-                                 h->pos4, h->vel4, h->cell_s, h->mend);
+                                 h->pos4, h->vel4, h->cell_s);
     else
         launch_rank_gather(st, h->precision, n, h->cap, h->cellof, h->start, h->key, h->src,
                            master(h, h->cur), master(h, 1 - h->cur), gather_a, h->geo, h->ph,
-                           h->pos4, h->vel4, h->cell_s, h->mend);
+                           h->pos4, h->vel4, h->cell_s);
     h->cur = 1 - h->cur;
 }
 
+bool use_split(const mdpd_handle* h);
+
 // Kernel launches of one time step (enqueue_step): count, scan, scatter,
-// rank + gather, density, force, reduction.
+// rank + gather, density (two under the frozen split), force, reduction.
 int step_launches(const mdpd_handle* h)
 {
-    return 6 + scan_num_launches(h->geo.ncell);
+    return 6 + scan_num_launches(h->geo.ncell) + (use_split(h) ? 1 : 0);
 }
 
 // The thread-per-particle density pass of a system with frozen particles
@@ -495,7 +504,7 @@ void ensure_ff(mdpd_handle* h)
 {
     if (!use_split(h) || !h->ff_dirty) return;
     launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
-                      h->cell_s, h->start, h->rho, h->nl, h->nl_count, 2, h->mend, h->id[h->cur],
+                      h->cell_s, h->start, h->rho, h->nl, h->nl_count, 2, h->facc, h->id[h->cur],
                       h->rho_ff);
     h->ff_dirty = false;
 }
@@ -520,7 +529,7 @@ void enqueue_density(mdpd_handle* h, bool all = false)
     if (h->want_phi || h->kernels == MDPD_KERNELS_NLIST_THREAD)
         // (the wall density is accumulated by this variant only)
         launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
-                          h->cell_s, h->start, h->rho, h->nl, h->nl_count, fs, h->mend,
+                          h->cell_s, h->start, h->rho, h->nl, h->nl_count, fs, h->facc,
                           h->id[h->cur], h->rho_ff, h->thread_shape);
     else if (cell)
         launch_density_cell(h->stream, h->precision, h->geo.ncell, h->cap, h->geo, h->ph, h->pos4,
@@ -555,8 +564,10 @@ void enqueue_reduce(mdpd_handle* h, int advance, cudaStream_t st = nullptr)
                                 h->d_wr, h->nrep, h->red_ticket, h->obs_b, h->step, advance);
         return;
     }
-    const int lpp = h->kernels == MDPD_KERNELS_SCAN ? 1 : h->force_lpp;
-    launch_reduce_obs(st, h->precision, h->partials, obs_num_partials((int)h->n, lpp),
+    const bool scan = h->kernels == MDPD_KERNELS_SCAN;
+    const int lpp = scan ? 1 : h->force_lpp;
+    const int rounds = scan ? 1 : force_nl_rounds(h->ph, lpp);
+    launch_reduce_obs(st, h->precision, h->partials, obs_num_partials((int)h->n, lpp, rounds),
                       h->red_l1,
                       h->red_ticket, h->obs, h->obs + MDPD_NUM_OBS, h->obs + 2 * MDPD_NUM_OBS,
                       h->step, advance);
@@ -789,7 +800,6 @@ int init_handle(mdpd_handle* h, const double* pos, const double* vel, const int3
     const int64_t nb = scan_num_blocks(h->geo.ncell);
     if ((rc = dalloc(h, &h->count, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->start, (size_t)(h->geo.ncell + 1) * sizeof(uint32_t))) ||
-        (rc = dalloc(h, &h->mend, (size_t)h->geo.ncell * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->scan_tmp, (size_t)(nb + 1) * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->tile_sums, (size_t)2 * nb * sizeof(uint32_t))) ||
         (rc = dalloc(h, &h->status, sizeof(uint32_t))) ||
@@ -1938,7 +1948,6 @@ void mdpd_destroy(mdpd_handle* h)
     free_particles(h);
     dfree(h->count);
     dfree(h->start);
-    dfree(h->mend);
     dfree(h->scan_tmp);
     dfree(h->tile_sums);
     dfree(h->status);

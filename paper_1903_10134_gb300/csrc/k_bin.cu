@@ -241,8 +241,7 @@ __global__ void k_cell_sort(int64_t ncell, const uint32_t* __restrict__ start,
 }
 
 // Order inside each cell by (frozen, particle id), fused with the gather into
-// cell order; the first particle of each cell also records where the cell's
-// frozen particles begin (mend).  The scatter filled slot a (in atomic order)
+// cell order.  The scatter filled slot a (in atomic order)
 // with key[a] = frozen << 31 | id and
 // src[a] = the particle's master index i; the particle's place in its cell c
 // is s = start[c] + (number of keys of the cell below key[a]), and the thread
@@ -256,7 +255,7 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
                               int gather_a, Geo geo_p, Phys ph_p, Batch bt,
                               typename Vec4<T>::type* __restrict__ pos4,
                               typename Vec4<T>::type* __restrict__ vel4,
-                              uint32_t* __restrict__ cell_s, uint32_t* __restrict__ mend)
+                              uint32_t* __restrict__ cell_s)
 {
     pdl_enter();
     int a;
@@ -284,15 +283,9 @@ __global__ void k_rank_gather(int n, int64_t cap, const uint32_t* __restrict__ c
     const uint32_t b = start[cg], e = start[cg + 1];
     if (e > (uint32_t)cap || b > e) return;
     const uint32_t kk = key[a];
-    uint32_t r = 0, nm = 0;
-    for (uint32_t q = b; q < e; ++q) {
-        const uint32_t kq = key[q];
-        r += kq < kk ? 1u : 0u;
-        nm += kq < 0x80000000u ? 1u : 0u;
-    }
+    uint32_t r = 0;
+    for (uint32_t q = b; q < e; ++q) r += key[q] < kk ? 1u : 0u;
     const uint32_t s = b + r;
-    // cells without particles keep a stale mend: readers clamp it to [b, e]
-    if (r == 0) mend[cg] = b + nm;
     const uint32_t c = cg - (uint32_t)cell0;      // cell within the replica
     const int q[3] = { (int)(c % (uint32_t)geo.nc[0]),
                        (int)((c / (uint32_t)geo.nc[0]) % (uint32_t)geo.nc[1]),
@@ -479,34 +472,33 @@ void launch_cell_sort(cudaStream_t st, int64_t ncell, const uint32_t* start, uin
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s,
-                        uint32_t* mend)
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s)
 {
     if (n <= 0) return;
     if (precision == 0)
         launch_pdl(k_rank_gather<double, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
                    start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (D4*)pos4, (D4*)vel4,
-                   cell_s, mend);
+                   cell_s);
     else
         launch_pdl(k_rank_gather<float, false>, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, cellof,
                    start, key, src, in, out, (int)gather_a, geo, ph, Batch{}, (float4*)pos4,
-                   (float4*)vel4, cell_s, mend);
+                   (float4*)vel4, cell_s);
 }
 
 void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
                               const uint32_t* start, const uint32_t* key, const uint32_t* src,
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
-                              void* pos4, void* vel4, uint32_t* cell_s, uint32_t* mend)
+                              void* pos4, void* vel4, uint32_t* cell_s)
 {
     if (bt.nchunk <= 0) return;
     const dim3 g(bt.nchunk), b(BATCH_CHUNK);
     if (precision == 0)
         launch_pdl_smem(k_rank_gather<double, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
-                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (D4*)pos4, (D4*)vel4, cell_s, mend);
+                        src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (D4*)pos4, (D4*)vel4, cell_s);
     else
         launch_pdl_smem(k_rank_gather<float, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
                         src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (float4*)pos4, (float4*)vel4,
-                        cell_s, mend);
+                        cell_s);
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,

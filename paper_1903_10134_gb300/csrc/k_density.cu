@@ -23,6 +23,41 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
     return (ox + 1) + 3 * (oy + 1) + 9 * (oz + 1);
 }
 
+// A scaled density term (at most 2^31 in FP32, 2^50 in FP64) rounded to the
+// nearest integer, and a fixed-point sum back in the pair precision.
+__device__ __forceinline__ unsigned long long to_fixed(float v)
+{
+    return (unsigned long long)__float2uint_rn(v);
+}
+__device__ __forceinline__ unsigned long long to_fixed(double v) { return __double2ull_rn(v); }
+__device__ __forceinline__ float from_fixed(unsigned long long a, float inv)
+{
+    const float hi = __uint2float_rn((uint32_t)(a >> 32));
+    const float lo = __uint2float_rn((uint32_t)a);
+    return fmaf(hi, 4294967296.0f, lo) * inv;
+}
+__device__ __forceinline__ double from_fixed(unsigned long long a, double inv)
+{
+    return __ull2double_rn(a) * inv;
+}
+
+// Densities of the frozen particles under the frozen split (see
+// k_density_nl): rho = frozen-frozen part + the mobile homes' scattered terms.
+template <typename T>
+__global__ void __launch_bounds__(PAIR_BLOCK)
+k_frozen_rho(int n, Phys ph, const uint32_t* __restrict__ id_s, const T* __restrict__ rho_ff,
+             unsigned long long* __restrict__ facc, T* __restrict__ rho_out)
+{
+    pdl_enter();
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const T f = rho_ff[id_s[s]];
+    if (f < T(0)) return;                       // a mobile particle
+    const unsigned long long a = facc[s];
+    rho_out[s] = f + from_fixed(a, derived<T>(ph).fix_inv);
+    if (a) facc[s] = 0ull;
+}
+
 // Thread-per-particle variant: each thread scans its 27 neighbour cells and
 // stores its partners straight to the slot-major list (no shared-memory
 // staging, so occupancy is set by registers alone).  The density term is
@@ -33,73 +68,36 @@ __device__ __forceinline__ int image_code(int ox, int oy, int oz)
 // Frozen split (FS, single systems with frozen particles).  Frozen particles
 // never move, so the part of a frozen particle's density that comes from
 // frozen neighbours is a constant: FS = 2 computes it once (frozen homes,
-// frozen candidates only) into rho_ff[id]; FS = 1 then scans only the mobile
-// slots [b, mend) of each neighbour cell for frozen homes and adds rho_ff.  With FS = 1 each block first moves its mobile homes
-// onto the leading lanes, so that warps of frozen homes run the short scans
-// together.  Homes with partner lists (mobile, or every home under list_all)
-// scan everything.
+// frozen candidates only) into rho_ff[id] (-1 for mobile ids).  FS = 1 then
+// scans for mobile homes only: a mobile home adds each frozen candidate's
+// share w_rho(r_ij) of that candidate's density (the same term it adds to its
+// own) to facc[j] as a fixed-point integer (Derived::fix_scale), by atomic
+// addition, so the sum does not depend on the order; k_frozen_rho then forms
+// rho_j = rho_ff + facc * fix_inv and clears facc.  Each FS = 1 block gathers
+// the mobile homes of FS_ROUNDS * PAIR_BLOCK slots and runs them in rounds of
+// PAIR_BLOCK, so no warp is spent on frozen homes.  Homes with partner lists
+// (mobile, or every home under list_all) scan everything.
 //
 // Two code shapes (SH, picked by the autotuner): 0 = candidate loop not
 // unrolled, registers as the compiler likes (faster on the porous rock);
 // 1 = unrolled by two with at least 8 resident blocks (faster on the batch of
 // slabs).  Their results are identical.
-template <typename T, bool BATCH, bool WANT_PHI, int FS, int SH>
-__global__ void __launch_bounds__(PAIR_BLOCK, SH ? 8 : 12)
-k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
-             const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
-             const uint32_t* __restrict__ start, T* __restrict__ rho_out,
-             uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count,
-             const uint32_t* __restrict__ mend, const uint32_t* __restrict__ id_s,
-             T* __restrict__ rho_ff)
+// Slots per block of the frozen-split pass, in units of PAIR_BLOCK: a block
+// gathers the mobile homes of FS_ROUNDS * PAIR_BLOCK slots and runs them in
+// rounds of PAIR_BLOCK, so its warps are full of mobile homes (on a porous
+// rock about 45 % of the slots are mobile, and a block of one PAIR_BLOCK
+// would keep most of its warps idle while holding its resident-block slot).
+constexpr int FS_ROUNDS = 4;
+
+// The density and partner list of the home in slot s (see k_density_nl).
+template <typename T, bool WANT_PHI, int FS, int SH>
+__device__ __forceinline__ void density_home(
+    int s, int64_t cap, const Geo& geo, const Phys& ph, int64_t cell0,
+    const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
+    const uint32_t* __restrict__ start, T* __restrict__ rho_out, uint32_t* __restrict__ nl,
+    uint32_t* __restrict__ nl_count, unsigned long long* __restrict__ facc,
+    const uint32_t* __restrict__ id_s, T* __restrict__ rho_ff)
 {
-    static_assert(FS == 0 || !BATCH, "the frozen split is for single systems");
-    pdl_enter();
-    int s;
-    bool valid;
-    int64_t cell0 = 0;
-    const Rep* rp = nullptr;
-    if constexpr (BATCH) {
-        const int4 ch = bt.chunks[blockIdx.x];
-        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
-        s = ch.y + (int)threadIdx.x;
-        valid = (int)threadIdx.x < ch.z;
-        cell0 = rp->cell0;
-    } else {
-        s = blockIdx.x * blockDim.x + threadIdx.x;
-        valid = s < n;
-    }
-    if constexpr (FS == 1) {
-        // mobile homes first, then frozen ones, each in slot order
-        __shared__ int act[PAIR_BLOCK];
-        __shared__ uint32_t wcnt[2][PAIR_BLOCK / 32];
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-        const bool mob = valid && (ph_p.list_all ||
-                                   ((ph_p.frozen >> unpack_u32(pos4[s].w)) & 1u) == 0u);
-        const unsigned bm = __ballot_sync(0xffffffffu, mob);
-        const unsigned bf = __ballot_sync(0xffffffffu, valid && !mob);
-        if (lane == 0) {
-            wcnt[0][warp] = (uint32_t)__popc(bm);
-            wcnt[1][warp] = (uint32_t)__popc(bf);
-        }
-        __syncthreads();
-        uint32_t om = 0, of = 0, nmob = 0, nall = 0;
-#pragma unroll
-        for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
-            om += w < warp ? wcnt[0][w] : 0u;
-            of += w < warp ? wcnt[1][w] : 0u;
-            nmob += wcnt[0][w];
-            nall += wcnt[0][w] + wcnt[1][w];
-        }
-        const unsigned lt = (1u << lane) - 1u;
-        if (mob) act[om + __popc(bm & lt)] = s;
-        else if (valid) act[nmob + of + __popc(bf & lt)] = s;
-        __syncthreads();
-        valid = threadIdx.x < nall;
-        if (valid) s = act[threadIdx.x];
-    }
-    if (!valid) return;
-    const Geo& geo = BATCH ? rp->geo : geo_p;
-    const Phys& ph = BATCH ? rp->ph : ph_p;
     const Derived<T>& dc = derived<T>(ph);
     const T rd2 = dc.rd2, rc2 = dc.rc2;
     const T inv_rd = dc.inv_rd;
@@ -107,7 +105,15 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     const auto pi = pos4[s];
     const bool mob_true = ((ph.frozen >> unpack_u32(pi.w)) & 1u) == 0u;
     const bool mobile = ph.list_all || mob_true;
-    if (FS == 2 && mobile) return;              // the frozen-frozen part only
+    if (FS == 2 && mobile) {                    // the frozen-frozen part only
+        rho_ff[id_s[s]] = T(-1);
+        return;
+    }
+    if (FS == 1 && !mobile) {                   // k_frozen_rho forms the density
+        nl_count[s] = 0;
+        if (WANT_PHI) ((T*)ph.phi_out)[s] = T(0);
+        return;
+    }
     // wall density of a mobile particle (WANT_PHI): sum over frozen partners
     // within r_c of 15/(2 pi r_c^3) (1 - r/r_c)^2
     const bool want_phi = WANT_PHI && mob_true;
@@ -137,7 +143,6 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 const uint32_t nc = (uint32_t)(cell0 + x + geo.nc[0] * (y + geo.nc[1] * z));
                 uint32_t b = start[nc], e = start[nc + 1];
                 if (!MDPD_DBG_OK(b <= e && e <= (uint32_t)cap, ph.dbg_status)) e = b;
-                if (FS == 1 && !mobile) e = min(max(mend[nc], b), e);     // mobile slots
                 // the common path is one distance test: r_d <= r_c, so the
                 // density term and the list append sit inside the r < r_c
                 // branch (about 15 % of the candidates); inside it the density
@@ -151,7 +156,10 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                     // depend on the frozen types the binning ordered by)
                     if (r2 < rc2 && (FS != 2 || ((ph.frozen >> unpack_u32(pj.w)) & 1u))) {
                         const T w = max(T(1) - sqrt_fast(r2) * inv_rd, T(0));
-                        acc += cw * w * w;              // r = 0 gives w(0)
+                        const T term = cw * w * w;      // r = 0 gives w(0)
+                        acc += term;
+                        if (FS == 1 && term > T(0) && ((ph.frozen >> unpack_u32(pj.w)) & 1u))
+                            atomicAdd(facc + j, to_fixed(term * dc.fix_scale));
                         if (mobile && r2 > T(0)) {      // not the home, not coincident
                             if (cnt < NL_MAX) {
                                 *lp = (j << 5) | code;
@@ -168,15 +176,89 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
             }
         }
     }
+    if (!ph.rho_self) acc -= cw;
     if constexpr (FS == 2) {
-        rho_ff[id_s[s]] = acc;                  // with the home's own w(0)
+        rho_ff[id_s[s]] = acc;
         return;
     }
-    if (FS == 1 && !mobile) acc += rho_ff[id_s[s]];
-    if (!ph.rho_self) acc -= cw;
     rho_out[s] = acc;
     nl_count[s] = cnt;
     if (WANT_PHI) ((T*)ph.phi_out)[s] = phi;
+}
+
+template <typename T, bool BATCH, bool WANT_PHI, int FS, int SH>
+__global__ void __launch_bounds__(PAIR_BLOCK, SH ? 8 : 12)
+k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
+             const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
+             const uint32_t* __restrict__ start, T* __restrict__ rho_out,
+             uint32_t* __restrict__ nl, uint32_t* __restrict__ nl_count,
+             unsigned long long* __restrict__ facc, const uint32_t* __restrict__ id_s,
+             T* __restrict__ rho_ff)
+{
+    static_assert(FS == 0 || !BATCH, "the frozen split is for single systems");
+    pdl_enter();
+    if constexpr (FS == 1) {
+        // the mobile homes of the block's FS_ROUNDS * PAIR_BLOCK slots, in
+        // slot order; frozen homes only clear their count (k_frozen_rho forms
+        // their density)
+        __shared__ int act[FS_ROUNDS * PAIR_BLOCK];
+        __shared__ uint32_t wcnt[FS_ROUNDS][PAIR_BLOCK / 32];
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const unsigned lt = (1u << lane) - 1u;
+        const int64_t base = (int64_t)blockIdx.x * (FS_ROUNDS * PAIR_BLOCK);
+        unsigned bm[FS_ROUNDS];
+#pragma unroll
+        for (int r = 0; r < FS_ROUNDS; ++r) {
+            const int64_t t = base + r * PAIR_BLOCK + threadIdx.x;
+            const bool valid = t < n;
+            bool mob = false;
+            if (valid) {
+                mob = ph_p.list_all || ((ph_p.frozen >> unpack_u32(pos4[t].w)) & 1u) == 0u;
+                if (!mob) {
+                    nl_count[t] = 0;
+                    if (WANT_PHI) ((T*)ph_p.phi_out)[t] = T(0);
+                }
+            }
+            bm[r] = __ballot_sync(0xffffffffu, mob);
+            if (lane == 0) wcnt[r][warp] = (uint32_t)__popc(bm[r]);
+        }
+        __syncthreads();
+        uint32_t nmob = 0;
+#pragma unroll
+        for (int r = 0; r < FS_ROUNDS; ++r) {
+            uint32_t off = nmob;
+#pragma unroll
+            for (int w = 0; w < PAIR_BLOCK / 32; ++w) {
+                off += w < warp ? wcnt[r][w] : 0u;
+                nmob += wcnt[r][w];
+            }
+            if ((bm[r] >> lane) & 1u)
+                act[off + __popc(bm[r] & lt)] = (int)(base + r * PAIR_BLOCK + threadIdx.x);
+        }
+        __syncthreads();
+        for (uint32_t q = threadIdx.x; q < nmob; q += PAIR_BLOCK)
+            density_home<T, WANT_PHI, FS, SH>(act[q], cap, geo_p, ph_p, 0, pos4, cell_s, start,
+                                              rho_out, nl, nl_count, facc, id_s, rho_ff);
+        return;
+    }
+    int s;
+    bool valid;
+    int64_t cell0 = 0;
+    const Rep* rp = nullptr;
+    if constexpr (BATCH) {
+        const int4 ch = bt.chunks[blockIdx.x];
+        rp = &block_rep<REP_SCALARS>(bt.reps, ch.x);
+        s = ch.y + (int)threadIdx.x;
+        valid = (int)threadIdx.x < ch.z;
+        cell0 = rp->cell0;
+    } else {
+        s = blockIdx.x * blockDim.x + threadIdx.x;
+        valid = s < n;
+    }
+    if (!valid) return;
+    density_home<T, WANT_PHI, FS, SH>(s, cap, BATCH ? rp->geo : geo_p, BATCH ? rp->ph : ph_p,
+                                      cell0, pos4, cell_s, start, rho_out, nl, nl_count, facc,
+                                      id_s, rho_ff);
 }
 
 // Warp-cooperative density pass: one warp per home cell.  The 27 neighbour
@@ -383,28 +465,33 @@ k_density_cell(int64_t ncell, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
 template <typename T, int SH>
 void density_nl_t(cudaStream_t st, int n, int64_t cap, const Geo& geo, const Phys& ph,
                   const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho,
-                  uint32_t* nl, uint32_t* nl_count, int fs, const uint32_t* mend,
+                  uint32_t* nl, uint32_t* nl_count, int fs, unsigned long long* facc,
                   const uint32_t* id_s, void* rho_ff)
 {
     using V = typename Vec4<T>::type;
     const int nb = (n + PAIR_BLOCK - 1) / PAIR_BLOCK;
+    const int nb1 = (n + FS_ROUNDS * PAIR_BLOCK - 1) / (FS_ROUNDS * PAIR_BLOCK);
     const bool phi = ph.phi_out != nullptr;
     auto k = phi ? k_density_nl<T, false, true, 0, SH> : k_density_nl<T, false, false, 0, SH>;
     if (fs == 1) k = phi ? k_density_nl<T, false, true, 1, SH> : k_density_nl<T, false, false, 1, SH>;
     if (fs == 2) k = k_density_nl<T, false, false, 2, SH>;
-    launch_pdl(k, dim3(nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{}, (const V*)pos4, cell_s,
-               start, (T*)rho, nl, nl_count, mend, id_s, (T*)rho_ff);
+    launch_pdl(k, dim3(fs == 1 ? nb1 : nb), dim3(PAIR_BLOCK), st, n, cap, geo, ph, Batch{},
+               (const V*)pos4, cell_s, start, (T*)rho, nl, nl_count, facc, id_s, (T*)rho_ff);
+    if (fs == 1)
+        launch_pdl(k_frozen_rho<T>, dim3(nb), dim3(PAIR_BLOCK), st, n, ph, id_s,
+                   (const T*)rho_ff, facc, (T*)rho);
 }
 
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
                        const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
-                       int fs, const uint32_t* mend, const uint32_t* id_s, void* rho_ff, int shape)
+                       int fs, unsigned long long* facc, const uint32_t* id_s, void* rho_ff,
+                       int shape)
 {
     if (n <= 0) return;
     auto f = precision == 0 ? (shape ? density_nl_t<double, 1> : density_nl_t<double, 0>)
                             : (shape ? density_nl_t<float, 1> : density_nl_t<float, 0>);
-    f(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, mend, id_s, rho_ff);
+    f(st, n, cap, geo, ph, pos4, cell_s, start, rho, nl, nl_count, fs, facc, id_s, rho_ff);
 }
 
 void launch_density_nl_batch(cudaStream_t st, int precision, int64_t cap, const Batch& bt,

@@ -341,13 +341,16 @@ void launch_force_t(cudaStream_t st, ForceMode mode, int n, int64_t cap, const G
 
 }  // namespace
 
-int force_num_blocks(int n, int lpp)
+int force_num_blocks(int n, int lpp, int rounds)
 {
-    const int per = PAIR_BLOCK / lpp;
+    const int per = PAIR_BLOCK / lpp * rounds;
     return n > 0 ? (n + per - 1) / per : 1;
 }
 
-int obs_num_partials(int n, int lpp) { return force_num_blocks(n, lpp) * (PAIR_BLOCK / 32); }
+int obs_num_partials(int n, int lpp, int rounds)
+{
+    return force_num_blocks(n, lpp, rounds) * (PAIR_BLOCK / 32);
+}
 
 void launch_density(cudaStream_t st, int precision, int n, const Geo& geo, const Phys& ph,
                     const void* pos4, const uint32_t* cell_s, const uint32_t* start, void* rho)

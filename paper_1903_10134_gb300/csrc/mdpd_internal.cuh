@@ -58,6 +58,8 @@ struct Derived {
     T c0[3];         // centre of cell 0: lo + h / 2
     T h_lo[3];       // FP32: h - h, c0 - c0 in FP64, rounded (h, c0 as FP32 pairs);
     T c0_lo[3];      //   FP64: zero
+    T fix_scale;     // 2^e: density terms as integers (frozen split), with
+    T fix_inv;       //   cw_rho * 2^e <= 2^31 (FP32) or 2^50 (FP64); and 2^-e
 };
 
 // Physical constants of Sec. 2.1 / Eq. 1, tables flattened [ti * 8 + tj].
@@ -112,7 +114,15 @@ inline void fill_derived(Phys& ph, const Geo& geo)
         const double span = (std::fabs(geo.lo[k]) + geo.L[k]) * geo.inv_h[k];
         if (geo.nc[k] <= 1024 && span <= 2048.0) ph.fast_cell |= 1u << k;
     }
+    // fixed-point scale of the frozen split's scattered density terms (each
+    // at most cw_rho): a power of two, so the scaling is exact
+    const int e64 = (int)std::floor(std::log2(std::ldexp(1.0, 50) / d.cw_rho));
+    const int e32 = (int)std::floor(std::log2(std::ldexp(1.0, 31) / d.cw_rho));
+    d.fix_scale = std::ldexp(1.0, e64);
+    d.fix_inv = std::ldexp(1.0, -e64);
     Derived<float>& f = ph.df;
+    f.fix_scale = (float)std::ldexp(1.0, e32);
+    f.fix_inv = (float)std::ldexp(1.0, -e32);
     f.rc2 = (float)d.rc2;
     f.rd2 = (float)d.rd2;
     f.inv_rc = (float)d.inv_rc;
@@ -280,17 +290,15 @@ void launch_scan_from_sums(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* o
 // For every scattered slot a: the particle's place s in its cell (rank of
 // key[a] = frozen << 31 | id among the cell's keys), and the gather of master
 // state in[src[a]] to out[s] with the cell-ordered compute arrays (pos4, vel4,
-// cell_s).  mend[c]: first frozen slot of every non-empty cell c (stale for
-// empty cells: clamp to [start[c], start[c + 1]]).
+// cell_s).
 void launch_rank_gather(cudaStream_t st, int precision, int n, int64_t cap,
                         const uint32_t* cellof, const uint32_t* start, const uint32_t* key,
                         const uint32_t* src, const Master& in, const Master& out, bool gather_a,
-                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s,
-                        uint32_t* mend);
+                        const Geo& geo, const Phys& ph, void* pos4, void* vel4, uint32_t* cell_s);
 void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const uint32_t* cellof,
                               const uint32_t* start, const uint32_t* key, const uint32_t* src,
                               const Master& in, const Master& out, bool gather_a, const Batch& bt,
-                              void* pos4, void* vel4, uint32_t* cell_s, uint32_t* mend);
+                              void* pos4, void* vel4, uint32_t* cell_s);
 void launch_bin_scatter(cudaStream_t st, int n, const uint32_t* cellof, const uint32_t* slot,
                         const uint32_t* start, const uint32_t* id, uint32_t* key, uint32_t* src,
                         uint32_t* status);
@@ -306,21 +314,28 @@ void launch_force(cudaStream_t st, int precision, ForceMode mode, int n, int64_t
                   const void* vel4, const void* rho, const uint32_t* cell_s,
                   const uint32_t* start, const uint64_t* step_ptr, int step_offset,
                   const Master& m, double* out, double* partials, uint32_t* status);
-// Blocks of a force launch over n particles at lpp lanes per particle.
-int force_num_blocks(int n, int lpp = 1);
+// Blocks of a force launch over n particles at lpp lanes per particle, each
+// block taking `rounds` rounds of its particles (see force_nl_rounds).
+int force_num_blocks(int n, int lpp = 1, int rounds = 1);
 // Number of per-warp observable partials the force pass writes for n particles.
-int obs_num_partials(int n, int lpp = 1);
+int obs_num_partials(int n, int lpp = 1, int rounds = 1);
+// Rounds per block of the list force pass of a single system (FORCE_ROUNDS
+// with frozen particles at one lane per particle, else 1).
+constexpr int FORCE_ROUNDS = 4;
+int force_nl_rounds(const Phys& ph, int lpp);
 // Density pass that also writes the force partners of mobile particles
 // (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
-// fs (frozen split; mend from the binning, id_s the cell-ordered ids, rho_ff
-// cap values of the pass's type indexed by id): 0 full scans; 2 writes the
-// frozen-frozen part of every frozen particle's density to rho_ff; 1 scans
-// only mobile candidates for frozen homes and adds rho_ff.
+// fs (frozen split; id_s the cell-ordered ids, rho_ff cap values of the
+// pass's type indexed by id, facc cap fixed-point accumulators in cell order,
+// zero between passes): 0 full scans; 2 writes the frozen-frozen part of
+// every frozen particle's density to rho_ff (-1 for mobile ids); 1 scans for
+// mobile homes only, which scatter their terms to frozen candidates into
+// facc, and a second launch forms the frozen densities and clears facc.
 void launch_density_nl(cudaStream_t st, int precision, int n, int64_t cap, const Geo& geo,
                        const Phys& ph, const void* pos4, const uint32_t* cell_s,
                        const uint32_t* start, void* rho, uint32_t* nl, uint32_t* nl_count,
-                       int fs = 0, const uint32_t* mend = nullptr, const uint32_t* id_s = nullptr,
-                       void* rho_ff = nullptr, int shape = 0);
+                       int fs = 0, unsigned long long* facc = nullptr,
+                       const uint32_t* id_s = nullptr, void* rho_ff = nullptr, int shape = 0);
 // Warp-per-cell variant of launch_density_nl (same outputs).
 void launch_density_cell(cudaStream_t st, int precision, int64_t ncell, int64_t cap,
                          const Geo& geo, const Phys& ph, const void* pos4, const uint32_t* start,

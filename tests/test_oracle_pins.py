@@ -290,7 +290,7 @@ def test_oracle_results_do_not_depend_on_thread_count():
     O.set_num_threads(n0)
     for u, v in zip(*out):
         assert np.array_equal(u, v)
-
+# --- the subset force routine that gives the full-size expected values -------------
 
 # --- the subset force routine used as the checker at full size ----------------------
 
@@ -328,7 +328,7 @@ def _subset_cases():
 
 @pytest.mark.parametrize("use_cells", [False, True])
 def test_forces_subset_equals_full_forces_bitwise(use_cells):
-    """orc_forces_subset, the checker of every full-size sampled parity test,
+    """orc_forces_subset, which gives the expected values of every full-size sampled parity test,
     is a second loop over the same candidates; on every sampled particle it
     must give exactly the accelerations of orc_forces (Sec. 2.1, Eq. 1), with
     the same summation order, so the two may not differ in a single bit."""
