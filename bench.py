@@ -579,11 +579,16 @@ def run_ours(args):
         chosen, tms = res
         tuned = {"chosen": {mdpd.KERNELS_NLIST: "nlist", mdpd.KERNELS_NLIST_THREAD: "nlist-thread"}[chosen],
                  "density_ms": {"nlist": tms[0], "nlist-thread": tms[1]},
+                 "density_shape": res.shape,
                  "force_lanes": res.lanes,
                  "force_ms": {str(l): t for l, t in zip((1, 2, 4), res.force_ms) if t >= 0}}
     elif args.kernels != "nlist":
         s.set_option(mdpd.OPT_KERNELS, {"scan": mdpd.KERNELS_SCAN,
                                         "nlist-thread": mdpd.KERNELS_NLIST_THREAD}[args.kernels])
+    if args.kernels != "auto" and args.density_shape is not None:
+        s.set_option(mdpd.OPT_DENSITY_SHAPE, args.density_shape)
+    if args.kernels != "auto" and args.force_lanes is not None:
+        s.set_option(mdpd.OPT_FORCE_LANES, args.force_lanes)
     n = s.n
     working_set = n * (16 + 16 + 4 + 4 + 2 * 3 * 24 + 8)
     flush = working_set < 4 * L2_BYTES
@@ -839,6 +844,11 @@ def main():
     ap.add_argument("--nvox", type=int, default=256, help="rock image edge in voxels")
     ap.add_argument("--nrep", type=int, default=256, help="replicas of the batch workload")
     ap.add_argument("--kernels", choices=("auto", "nlist", "nlist-thread", "scan"), default="auto")
+    ap.add_argument("--density-shape", type=int, choices=(0, 1), default=None,
+                    help="code shape of the thread-per-particle density kernel when "
+                         "--kernels is not auto")
+    ap.add_argument("--force-lanes", type=int, choices=(1, 2, 4), default=None,
+                    help="lanes per particle of the force pass when --kernels is not auto")
     ap.add_argument("--profile-every", type=int, default=10,
                     help="record per-kernel events on every k-th timed step")
     args = ap.parse_args()

@@ -379,11 +379,11 @@ int mdpd_window_vjp_dev(mdpd_handle* h, const double* xbar, const double* vbar,
  * in both code shapes of MDPD_OPT_DENSITY_SHAPE) and then the force pass at 1,
  * 2 and 4 lanes per particle (MDPD_OPT_FORCE_LANES; 1 only on a batch) on the
  * current state, reps launches each, and keep the fastest of each.  The
- * trajectory is not advanced.  chosen (may be NULL, 2 ints) receives the
- * density variant and the lanes per particle; ms (may be NULL, 5 doubles) the
- * mean time of each density variant in that order (the thread variant's
- * faster shape), then of the force pass at 1, 2, 4 lanes (-1: not tried).
- * Synchronises. */
+ * trajectory is not advanced.  chosen (may be NULL, 3 ints) receives the
+ * density variant, the lanes per particle and the code shape kept; ms (may be
+ * NULL, 5 doubles) the mean time of each density variant in that order (the
+ * thread variant's faster shape), then of the force pass at 1, 2, 4 lanes (-1:
+ * not tried).  Synchronises. */
 int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms);
 
 /* Grid of the cell lattice (cells per axis) and the kernel launches one step

@@ -509,6 +509,11 @@ void ensure_ff(mdpd_handle* h)
     h->ff_dirty = false;
 }
 
+// Partner lists indexed by compacted mobile position (ph.list_compact): the
+// frozen-split density pass and the force pass at one lane per particle use
+// the same blocks of FORCE_ROUNDS * PAIR_BLOCK slots.
+bool list_compact(const mdpd_handle* h) { return use_split(h) && h->force_lpp == 1; }
+
 // all: partner lists for every particle, frozen ones too (the adjoint's;
 // a single system takes it from ph.list_all).
 void enqueue_density(mdpd_handle* h, bool all = false)
@@ -525,6 +530,7 @@ void enqueue_density(mdpd_handle* h, bool all = false)
         return;
     }
     h->ph.phi_out = h->want_phi ? h->phi : nullptr;
+    h->ph.list_compact = list_compact(h) ? 1 : 0;
     const int fs = use_split(h) ? 1 : 0;
     if (h->want_phi || h->kernels == MDPD_KERNELS_NLIST_THREAD)
         // (the wall density is accumulated by this variant only)
@@ -545,12 +551,13 @@ void enqueue_force(mdpd_handle* h, ForceMode mode, int step_offset, double* out,
         launch_force_nl_batch(h->stream, h->precision, mode, h->cap, h->batch(), h->pos4, h->vel4,
                               h->rho, h->cell_s, h->start, h->nl, h->nl_count, h->step,
                               step_offset, master(h, h->cur), out, h->partials, h->status);
-    else if (h->kernels != MDPD_KERNELS_SCAN)
+    else if (h->kernels != MDPD_KERNELS_SCAN) {
+        h->ph.list_compact = list_compact(h) ? 1 : 0;
         launch_force_nl(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph,
                         h->force_lpp, h->mk,
                         h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->nl, h->nl_count,
                         h->step, step_offset, master(h, h->cur), out, h->partials, h->status);
-    else
+    } else
         launch_force(h->stream, h->precision, mode, (int)h->n, h->cap, h->geo, h->ph, h->mk,
                      h->pos4, h->vel4, h->rho, h->cell_s, h->start, h->step, step_offset,
                      master(h, h->cur), out, h->partials, h->status);
@@ -1912,6 +1919,7 @@ int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
             continue;
         }
         h->force_lpp = lanes[v];
+        enqueue_density(h);                   // lists in this setting's layout (untimed)
         const double t = time_it([&] { enqueue_force(h, FM_EVAL, 0, h->fout); });
         if (t < 0) return done(MDPD_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
         if (ms) ms[2 + v] = t;
@@ -1921,10 +1929,12 @@ int mdpd_autotune(mdpd_handle* h, int32_t reps, int32_t* chosen, double* ms)
         }
     }
     h->force_lpp = best_l;
+    enqueue_density(h);                       // lists in the chosen layout
     destroy_graphs(h);
     if (chosen) {
         chosen[0] = best;
         chosen[1] = best_l;
+        chosen[2] = h->thread_shape;
     }
     rc = done(MDPD_OK, "");
     if (rc) return rc;

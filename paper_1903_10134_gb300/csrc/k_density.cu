@@ -87,7 +87,7 @@ k_frozen_rho(int n, Phys ph, const uint32_t* __restrict__ id_s, const T* __restr
 // rounds of PAIR_BLOCK, so its warps are full of mobile homes (on a porous
 // rock about 45 % of the slots are mobile, and a block of one PAIR_BLOCK
 // would keep most of its warps idle while holding its resident-block slot).
-constexpr int FS_ROUNDS = 4;
+constexpr int FS_ROUNDS = FORCE_ROUNDS;      // the same blocks as the force pass's rounds
 
 // The density and partner list of the home in slot s (see k_density_nl).
 template <typename T, bool WANT_PHI, int FS, int SH>
@@ -96,7 +96,7 @@ __device__ __forceinline__ void density_home(
     const typename Vec4<T>::type* __restrict__ pos4, const uint32_t* __restrict__ cell_s,
     const uint32_t* __restrict__ start, T* __restrict__ rho_out, uint32_t* __restrict__ nl,
     uint32_t* __restrict__ nl_count, unsigned long long* __restrict__ facc,
-    const uint32_t* __restrict__ id_s, T* __restrict__ rho_ff)
+    const uint32_t* __restrict__ id_s, T* __restrict__ rho_ff, int64_t lcol)
 {
     const Derived<T>& dc = derived<T>(ph);
     const T rd2 = dc.rd2, rc2 = dc.rc2;
@@ -126,7 +126,7 @@ __device__ __forceinline__ void density_home(
     // off at the end unless the self term is asked for
     T acc = T(0);
     uint32_t cnt = 0;
-    uint32_t* lp = nl + s;                      // next list entry: nl[cnt * cap + s]
+    uint32_t* lp = nl + lcol;                   // next list entry: nl[cnt * cap + lcol]
     for (int oz = -1; oz <= 1; ++oz) {
         const int z = neighbour_index(q2, oz, geo.nc[2], geo.periodic[2]);
         if (z < 0) continue;
@@ -236,9 +236,14 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
                 act[off + __popc(bm[r] & lt)] = (int)(base + r * PAIR_BLOCK + threadIdx.x);
         }
         __syncthreads();
+        // list column: the home's slot, or (list_compact) the block's first
+        // slot plus the home's place among its mobile homes, which the force
+        // pass's rounds blocks form the same way (consecutive columns for a
+        // warp's homes: coalesced list stores and loads)
         for (uint32_t q = threadIdx.x; q < nmob; q += PAIR_BLOCK)
             density_home<T, WANT_PHI, FS, SH>(act[q], cap, geo_p, ph_p, 0, pos4, cell_s, start,
-                                              rho_out, nl, nl_count, facc, id_s, rho_ff);
+                                              rho_out, nl, nl_count, facc, id_s, rho_ff,
+                                              ph_p.list_compact ? base + q : (int64_t)act[q]);
         return;
     }
     int s;
@@ -258,7 +263,7 @@ k_density_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt,
     if (!valid) return;
     density_home<T, WANT_PHI, FS, SH>(s, cap, BATCH ? rp->geo : geo_p, BATCH ? rp->ph : ph_p,
                                       cell0, pos4, cell_s, start, rho_out, nl, nl_count, facc,
-                                      id_s, rho_ff);
+                                      id_s, rho_ff, s);
 }
 
 // Warp-cooperative density pass: one warp per home cell.  The 27 neighbour

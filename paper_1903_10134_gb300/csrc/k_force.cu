@@ -150,6 +150,11 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
             const uint32_t id_i = unpack_u32(vi.w);
             const V* tP = tab.P + ti * 8;
             const uint32_t cnt = nl_count[s];
+            // list column (see k_density_nl): the slot, or under list_compact
+            // (rounds blocks only) the block's first slot plus the place among
+            // its mobile particles, which the density pass formed the same way
+            const int64_t lcol = (FR > 1 && ph.list_compact)
+                                     ? (int64_t)blockIdx.x * (FR * PPB) + slot : (int64_t)s;
             if (cnt <= (uint32_t)NL_MAX) {
                 const uint32_t k0 = (uint32_t)sub;
                 // (debug build: an entry naming a slot beyond the arrays or a code
@@ -157,7 +162,7 @@ k_force_nl(int n, int64_t cap, Geo geo_p, Phys ph_p, Batch bt, MaskDev mk,
                 // stays inside the arrays; the result is then wrong and flagged)
                 auto entry = [&](uint32_t k) -> uint32_t {
                     if (k >= cnt) return 0u;
-                    const uint32_t e = nl[(int64_t)k * cap + s];
+                    const uint32_t e = nl[(int64_t)k * cap + lcol];
                     return MDPD_DBG_OK((e >> 5) < (uint32_t)cap && (e & 31u) < 27u, ph.dbg_status)
                                ? e : 0u;
                 };

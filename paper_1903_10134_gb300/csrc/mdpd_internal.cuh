@@ -71,6 +71,8 @@ struct Phys {
     int xi_dist;
     int rho_self;
     int list_all;                 // 1: the density pass lists partners of frozen particles too
+    int list_compact;             // 1: list column = block base + compacted mobile position
+                                  //    (frozen-split density pass and rounds force pass)
     int prec32;                   // 1: FP32 pair arithmetic (kick increments formed in FP32)
     uint32_t fast_cell;           // bit k: axis k may take cell indices in FP32 (see k_bin_count)
     void* phi_out;                // wall density output (cell order, FP32/FP64), or nullptr

@@ -447,11 +447,13 @@ class Tuned(tuple):
     """Result of mdpd_autotune: unpacks as (density variant, [ms of NLIST,
     NLIST_THREAD]);
     .lanes is the force pass's lanes per particle, .force_ms its times at 1, 2,
-    4 lanes (-1: not tried)."""
+    4 lanes (-1: not tried), .shape the thread-per-particle density kernel's
+    code shape (MDPD_OPT_DENSITY_SHAPE) kept by the tuner."""
 
     def __new__(cls, chosen, ms):
         t = super().__new__(cls, (int(chosen[0]), [float(x) for x in ms[:2]]))
         t.lanes = int(chosen[1])
+        t.shape = int(chosen[2])
         t.force_ms = [float(x) for x in ms[2:]]
         return t
 
@@ -459,7 +461,7 @@ class Tuned(tuple):
 def mdpd_autotune(h, reps: int = 5) -> Tuned:
     """Pick the faster density-pass variant, then the fastest lanes per
     particle of the force pass, on the current state."""
-    chosen = np.zeros(2, np.int32)
+    chosen = np.zeros(3, np.int32)
     ms = np.zeros(5)
     _check(lib().mdpd_autotune(h, int(reps), _p(chosen), _p(ms)), h)
     return Tuned(chosen, ms)

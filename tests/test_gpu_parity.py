@@ -49,15 +49,20 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("kernels", [0, 1, 2])
+# (kernel variant, code shape of the thread-per-particle density kernel)
+VARIANTS = [(0, 0), (1, 0), (2, 0), (2, 1)]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("case", CASES)
-def test_forces_and_density_match_oracle(M, case, precision, kernels):
+def test_forces_and_density_match_oracle(M, case, precision, variant):
     n, L, per, nt, seed = case
     w = I.tiny(n, L, seed, periodic=per, ntypes=nt, g=(0.01, -0.02, 0.005),
                frozen_types=(1,) if nt > 1 else ())
     s, p = make(M, w, precision)
-    s.set_option(M.OPT_KERNELS, kernels)
+    s.set_option(M.OPT_KERNELS, variant[0])
+    s.set_option(M.OPT_DENSITY_SHAPE, variant[1])
     f, rho = s.forces()
     o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
     assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * max(1.0, o.rho.max())
@@ -246,12 +251,15 @@ def test_workload_sampled_parity(M, name):
     s.close()
 
 
+@pytest.mark.parametrize("variant", [(0, 0), (2, 0), (2, 1)])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_dense_particles_overflow_the_list(M, precision):
+def test_dense_particles_overflow_the_list(M, precision, variant):
     """At density ~47 every particle has ~200 partners within r_c, more than the
     64 list slots: the force pass falls back to scanning the cells itself."""
     w = I.tiny(3000, (4.0, 4.0, 4.0), 31, ntypes=2, spread=0.5)
     s, p = make(M, w, precision)
+    s.set_option(M.OPT_KERNELS, variant[0])
+    s.set_option(M.OPT_DENSITY_SHAPE, variant[1])
     f, rho = s.forces()
     o = O.Oracle(p, w.pos, w.vel, w.type, w.seed)
     assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * o.rho.max()
@@ -495,29 +503,33 @@ def test_frozen_split_graph_direct_and_resume_bitwise(M, precision):
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("name", ["rock", "tiny"])
+@pytest.mark.parametrize("name", ["rock", "tiny", "dense"])
 def test_density_code_shapes_agree_bitwise(M, name, precision):
     """The two code shapes of the thread-per-particle density kernel compute
-    the same arithmetic: trajectories agree bit for bit."""
+    the same arithmetic: trajectories agree bit for bit, also in a dense box
+    (about 200 partners per particle, beyond the list slots)."""
     if name == "rock":
-        w, a = _rock_thread(M, precision)
-        _, b = _rock_thread(M, precision)
+        runs = [_rock_thread(M, precision)[1] for _ in range(2)]
     else:
-        w = I.tiny(3000, (8.0, 7.0, 7.5), 41, ntypes=2, g=(0.02, 0.0, 0.0))
-        a, _ = make(M, w, precision)
-        b, _ = make(M, w, precision)
-        for s in (a, b):
+        if name == "tiny":
+            w = I.tiny(3000, (8.0, 7.0, 7.5), 41, ntypes=2, g=(0.02, 0.0, 0.0))
+        else:
+            w = I.tiny(3000, (4.0, 4.0, 4.0), 31, ntypes=2, spread=0.5)
+        runs = [make(M, w, precision)[0] for _ in range(2)]
+        for s in runs:
             s.set_option(M.OPT_KERNELS, M.KERNELS_NLIST_THREAD)
-    b.set_option(M.OPT_DENSITY_SHAPE, 1)
+    for k, s in enumerate(runs):
+        s.set_option(M.OPT_DENSITY_SHAPE, k)
     with pytest.raises(M.MDPDError):
-        b.set_option(M.OPT_DENSITY_SHAPE, 2)
-    for s in (a, b):
+        runs[0].set_option(M.OPT_DENSITY_SHAPE, 2)
+    for s in runs:
         s.step(12)
-    xa, va, _, ra = a.state()
-    xb, vb, _, rb = b.state()
-    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
-    a.close()
-    b.close()
+    xa, va, _, ra = runs[0].state()
+    for s in runs[1:]:
+        xb, vb, _, rb = s.state()
+        assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(ra, rb)
+    for s in runs:
+        s.close()
 
 
 @pytest.mark.parametrize("name", ["rock", "slit"])
