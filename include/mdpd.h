@@ -185,7 +185,10 @@ int mdpd_get_state_dev(mdpd_handle* h, double* pos, double* vel, int32_t* type,
 
 /* Replace positions and velocities (3N doubles each, id order, host arrays);
  * types and step index are kept; densities and forces are re-evaluated at the
- * current step index.  Positions on periodic axes are wrapped into the box. */
+ * current step index.  Positions on periodic axes are wrapped into the box.
+ * The frozen-frozen part of the wall particles' densities is kept when every
+ * frozen particle is loaded at exactly the position it had when that part was
+ * computed, and recomputed otherwise.  Synchronises. */
 int mdpd_set_state(mdpd_handle* h, const double* pos, const double* vel);
 
 /* Device-array variant of mdpd_set_state. */

@@ -74,6 +74,10 @@ struct mdpd_handle {
     void* rho_ff = nullptr;
     unsigned long long* facc = nullptr;  // cap fixed-point density sums of the frozen split
     bool ff_dirty = true;
+    // positions (by id, n x 3) the frozen-frozen part was computed from, and a
+    // device word that set_state raises when a loaded frozen position differs
+    double* ffx = nullptr;
+    uint32_t* ff_moved = nullptr;
     // misc
     uint32_t* status = nullptr;
     uint64_t* step = nullptr;
@@ -225,6 +229,8 @@ void free_particles(mdpd_handle* h)
     dfree(h->phi);
     dfree(h->rho_ff);
     dfree(h->facc);
+    dfree(h->ffx);
+    dfree(h->ff_moved);
 }
 
 int alloc_particles(mdpd_handle* h, int64_t cap)
@@ -258,6 +264,8 @@ int alloc_particles(mdpd_handle* h, int64_t cap)
     if (!rc) rc = dalloc(h, &h->phi, c * tsz);
     if (!rc) rc = dalloc(h, &h->rho_ff, c * tsz);
     if (!rc) rc = dalloc(h, &h->facc, c * sizeof(unsigned long long));
+    if (!rc && !h->nrep) rc = dalloc(h, &h->ffx, 3 * c * sizeof(double));
+    if (!rc && h->ffx) rc = dalloc(h, &h->ff_moved, sizeof(uint32_t));
     if (!rc && cudaMemset(h->facc, 0, c * sizeof(unsigned long long)) != cudaSuccess)
         rc = h->fail(MDPD_ERR_CUDA, "cudaMemset of the frozen-split sums failed");
     if (!rc && cudaDeviceSynchronize() != cudaSuccess)
@@ -293,6 +301,8 @@ void swap_particle_arrays(mdpd_handle* a, mdpd_handle* b)
     std::swap(a->phi, b->phi);
     std::swap(a->rho_ff, b->rho_ff);
     std::swap(a->facc, b->facc);
+    std::swap(a->ffx, b->ffx);
+    std::swap(a->ff_moved, b->ff_moved);
     std::swap(a->cap, b->cap);
 }
 
@@ -367,6 +377,11 @@ void make_geo_phys(const mdpd_params& p, uint64_t seed, Geo& g, Phys& f)
         g.hi[k] = p.box_lo[k] + p.box[k];
         g.key_lo[k] = f64_key(g.lo[k]);
         g.key_hi[k] = f64_key(g.hi[k]);
+        // below hi by twice the spacing of doubles near the larger face: for
+        // lo <= x < hi_in the difference x - lo rounds to [0, L)
+        const double big = std::max(std::fabs(g.lo[k]), std::fabs(g.hi[k]));
+        const double hi_in = g.hi[k] - 2.0 * (std::nextafter(big, HUGE_VAL) - big);
+        g.key_in[k] = f64_key(hi_in > g.lo[k] ? hi_in : g.lo[k]);
         g.h[k] = p.box[k] / m;
         g.inv_h[k] = 1.0 / g.h[k];
         g.ncell *= m;
@@ -506,6 +521,9 @@ void ensure_ff(mdpd_handle* h)
     launch_density_nl(h->stream, h->precision, (int)h->n, h->cap, h->geo, h->ph, h->pos4,
                       h->cell_s, h->start, h->rho, h->nl, h->nl_count, 2, h->facc, h->id[h->cur],
                       h->rho_ff);
+    // the positions it was computed from (set_state keeps the part while the
+    // frozen particles are loaded unmoved)
+    if (h->ffx) launch_scatter_by_id(h->stream, (int)h->n, h->cap, h->id[h->cur], h->x[h->cur], h->ffx);
     h->ff_dirty = false;
 }
 
@@ -1368,18 +1386,34 @@ static int set_state_impl(mdpd_handle* h, const double* pos, const double* vel, 
     else
         launch_load_state(st, n, h->cap, d_pos, d_vel, d_acc, h->geo, master(h, c), h->type_by_id,
                           h->status);
-    h->ff_dirty = true;                      // the frozen particles may have moved
+    // the frozen-frozen density part stays valid if no frozen particle moved
+    // (a caller that resumes or steps a state it read back loads the walls
+    // unchanged): compared bit for bit with the positions it came from
+    if (use_split(h) && !h->ff_dirty && h->ffx && n > 0) {
+        CK(cudaMemsetAsync(h->ff_moved, 0, sizeof(uint32_t), st));
+        launch_frozen_moved(st, n, h->cap, h->x[c], h->ffx, h->type_by_id, h->ph.frozen,
+                            h->ff_moved);
+        uint32_t moved = 1;
+        CK(cudaMemcpyAsync(&moved, h->ff_moved, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        h->ff_dirty = moved != 0;
+    } else {
+        h->ff_dirty = true;
+    }
     if (acc) {
-        // no evaluation; a binning (the accelerations gathered along) gives
-        // the frozen-frozen density part its cell order
-        if (use_split(h)) {
+        // no evaluation; when the frozen-frozen part must be recomputed, a
+        // binning (the accelerations gathered along) gives it its cell order
+        if (use_split(h) && h->ff_dirty) {
             enqueue_bin(h, true);
             ensure_ff(h);
         }
         CK(cudaGetLastError());
-        return MDPD_OK;
+    } else if ((rc = evaluate(h, nullptr, false))) {
+        return rc;
     }
-    if ((rc = evaluate(h, nullptr, false))) return rc;
+    // host inputs are the caller's again when this returns (a copy from a
+    // page-locked buffer runs asynchronously)
+    if (!dev) CK(cudaStreamSynchronize(st));
     return MDPD_OK;
 }
 

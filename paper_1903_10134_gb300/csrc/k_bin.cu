@@ -363,10 +363,18 @@ __global__ void k_load_state(int n, int64_t cap, const double* __restrict__ pos3
         double x = pos3[3 * i + k];
         const double v = vel3[3 * i + k];
         if (!isfinite(x) || !isfinite(v)) st |= ST_NONFINITE;
-        if (geo.periodic[k] && isfinite(x)) {
-            const double w = floor((x - geo.lo[k]) / geo.L[k]);
-            if (w != 0.0) x -= geo.L[k] * w;      // in-box positions stay bit-identical
-            if (x >= geo.hi[k] || x < geo.lo[k]) x = geo.lo[k];
+        // a position in [lo, key_in) is left as it is (there x - lo rounds to
+        // [0, L), so the wrap below would not change it); the FP64 division
+        // runs only for the others, under a branch a warp takes when one of
+        // its lanes needs it (FP64 runs at 1/64 of the FP32 rate)
+        const int64_t kx = f64_key(x);
+        const bool wrap = geo.periodic[k] && isfinite(x) && (kx < geo.key_lo[k] || kx >= geo.key_in[k]);
+        if (__any_sync(__activemask(), wrap)) {
+            if (wrap) {
+                const double w = floor((x - geo.lo[k]) / geo.L[k]);
+                if (w != 0.0) x -= geo.L[k] * w;      // in-box positions stay bit-identical
+                if (x >= geo.hi[k] || x < geo.lo[k]) x = geo.lo[k];
+            }
         }
         m.x[k * cap + i] = x;
         m.v[k * cap + i] = v;
@@ -499,6 +507,28 @@ void launch_rank_gather_batch(cudaStream_t st, int precision, int64_t cap, const
         launch_pdl_smem(k_rank_gather<float, true>, g, b, REP_SMEM, st, 0, cap, cellof, start, key,
                         src, in, out, (int)gather_a, Geo{}, Phys{}, bt, (float4*)pos4, (float4*)vel4,
                         cell_s);
+}
+
+__global__ void k_frozen_moved(int n, int64_t cap, const double* __restrict__ x,
+                               const double* __restrict__ ref, const uint8_t* __restrict__ type_by_id,
+                               uint32_t frozen, uint32_t* __restrict__ moved)
+{
+    pdl_enter();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !((frozen >> type_by_id[i]) & 1u)) return;
+    bool diff = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        diff |= __double_as_longlong(x[k * cap + i]) != __double_as_longlong(ref[3 * i + k]);
+    if (diff) atomicOr(moved, 1u);
+}
+
+void launch_frozen_moved(cudaStream_t st, int n, int64_t cap, const double* x, const double* ref,
+                         const uint8_t* type_by_id, uint32_t frozen, uint32_t* moved)
+{
+    if (n <= 0) return;
+    launch_pdl(k_frozen_moved, dim3(nblocks(n)), dim3(BLOCK), st, n, cap, x, ref, type_by_id,
+               frozen, moved);
 }
 
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,

@@ -37,6 +37,8 @@ struct Geo {
     int periodic[3];
     double lo[3], L[3], hi[3], h[3], inv_h[3];
     int64_t key_lo[3], key_hi[3];   // f64_key(lo), f64_key(hi): face comparisons in integers
+    int64_t key_in[3];              // f64_key of a bound below hi: lo <= x below it implies
+                                    //   0 <= RN(x - lo) < L (a loaded position needs no wrap)
     int64_t ncell;
 };
 
@@ -449,6 +451,12 @@ void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const
                                int32_t* out);
 // Master state in id order from pos3, vel3 and (if not NULL) acc3, all
 // interleaved xyz; periodic axes wrapped.
+// Set *moved (device word, not cleared here) to 1 if a frozen particle's
+// loaded position (master arrays indexed by id, as k_load_state leaves them)
+// differs in any bit from ref (n x 3, by id), the positions the frozen-frozen
+// density part was computed from.
+void launch_frozen_moved(cudaStream_t st, int n, int64_t cap, const double* x, const double* ref,
+                         const uint8_t* type_by_id, uint32_t frozen, uint32_t* moved);
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
                        const double* vel3, const double* acc3, const Geo& geo, const Master& m,
                        const uint8_t* type_by_id, uint32_t* status);

@@ -559,3 +559,63 @@ def test_full_walled_workload_sampled_parity(M, name):
     assert err.max() <= TOL[1], err.max()
     assert np.all(f[t == w.wall_type] == 0)
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_set_state_with_moved_walls_recomputes_frozen_part(M, precision):
+    """set_state keeps the frozen-frozen density part only while every frozen
+    particle is loaded at the bits it was computed from: one wall particle
+    moved by a small step changes the walls' densities, which then equal the
+    oracle's at the new state; loading the state unchanged keeps them."""
+    w, s = _rock_thread(M, precision)
+    s.step(4)
+    x, v, t, _ = s.state()
+    acc = M.mdpd_get_accel(s.h)
+    walls = np.flatnonzero(t == w.wall_type)
+    x2 = x.copy()
+    x2[walls[len(walls) // 2]] += np.array([0.05, -0.03, 0.02])
+    for xs in (x, x2, x2, x):
+        M.mdpd_set_state_accel(s.h, xs, v, acc)
+        f, rho = s.forces()
+        o = O.Oracle(w.params.copy(precision=0), xs, v, t, w.seed, use_cells=True,
+                     step=M.mdpd_step_count(s.h))
+        assert np.abs(rho - o.rho).max() <= RHO_TOL[precision] * max(1.0, o.rho.max())
+        mob = t != w.wall_type
+        assert rel_force_err(f[mob], o.a[mob]) <= TOL[precision]
+    s.close()
+
+
+def test_loaded_positions_wrap_like_the_periodic_rule(M):
+    """Positions loaded on a periodic axis are wrapped by x - L floor((x -
+    lo) / L), and onto lo if the result leaves [lo, hi): in-box positions
+    (also those just below hi, where x - lo can round to L) keep their bits.
+    Checked against the same FP64 rule in numpy, on a box with lo != 0, for
+    positions at most one box length out (there L * floor(...) is exact, so
+    the rule has one rounding however the product and difference are
+    contracted)."""
+    lo = np.array([-3.3, 0.7, -100.1])
+    L = np.array([7.3, 6.0, 9.9])
+    hi = lo + L
+    p = I.MDPDParams(box_lo=tuple(lo), box=tuple(L))
+    rng = np.random.default_rng(8)
+    x = lo + rng.random((600, 3)) * L
+    k = 0
+    for ax in range(3):
+        for val in (lo[ax], np.nextafter(lo[ax], np.inf), np.nextafter(lo[ax], -np.inf),
+                    hi[ax], np.nextafter(hi[ax], -np.inf),
+                    np.nextafter(np.nextafter(hi[ax], -np.inf), -np.inf),
+                    hi[ax] + 0.25 * L[ax], lo[ax] - 0.25 * L[ax], lo[ax] - 0.75 * L[ax]):
+            x[k, ax] = val
+            k += 1
+    want = x.copy()
+    for ax in range(3):
+        c = want[:, ax]
+        wv = np.floor((c - lo[ax]) / L[ax])
+        c = np.where(wv != 0.0, c - L[ax] * wv, c)
+        c = np.where((c >= hi[ax]) | (c < lo[ax]), lo[ax], c)
+        want[:, ax] = c
+    n = x.shape[0]
+    with M.System(p, lo + 0.5 * L + np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n, np.int32), 3) as s:
+        M.mdpd_set_state_accel(s.h, x, np.zeros((n, 3)), np.zeros((n, 3)))
+        got = s.state()[0]
+    assert np.array_equal(got.view(np.int64), want.view(np.int64))
