@@ -9,9 +9,12 @@
 // pass (k_force.cu) runs the pair force only for real partners.  A list entry
 // is (j << 5) | image code, where the code (0..26) names the neighbour cell
 // offset (ox, oy, oz) that fixes the periodic image of j; so j < 2^27.
-// Lists are slot-major (nl[k * cap + i]) so consecutive particles store
-// consecutive words.  Particles with more than NL_MAX partners keep only the
-// count, and the force pass scans their cells directly.
+// Lists are slot-major (nl[k * cap + column]) so consecutive particles store
+// consecutive words; the column is the particle's slot, or, under
+// ph.list_compact (frozen-split pass), its block's first slot plus its place
+// among the block's mobile particles.  Particles with more than NL_MAX
+// partners keep only the count, and the force pass scans their cells
+// directly.
 #include "pair.cuh"
 
 namespace mdpd {

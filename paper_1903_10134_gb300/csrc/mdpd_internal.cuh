@@ -328,7 +328,8 @@ int obs_num_partials(int n, int lpp = 1, int rounds = 1);
 constexpr int FORCE_ROUNDS = 4;
 int force_nl_rounds(const Phys& ph, int lpp);
 // Density pass that also writes the force partners of mobile particles
-// (entries (j << 5) | image code, slot-major: nl[k * cap + i]; nl_count[i]).
+// (entries (j << 5) | image code, slot-major: nl[k * cap + column] with the
+// column of ph.list_compact; nl_count[i] by slot).
 // fs (frozen split; id_s the cell-ordered ids, rho_ff cap values of the
 // pass's type indexed by id, facc cap fixed-point accumulators in cell order,
 // zero between passes): 0 full scans; 2 writes the frozen-frozen part of
