@@ -150,8 +150,9 @@ int mdpd_batch_set_params(mdpd_handle* h, const mdpd_params* params);
  *    (voxel id, k, 0x57414C4C, 0); they take ids n, n+1, ... by ascending
  *    voxel id.  Their velocity is 0.
  * May be called once per handle.  Densities and forces are re-evaluated.
- * Errors: INVALID_ARG (dims, voxel, type, a periodic axis the image does not
- * span exactly, a second call), OOM, CUDA. */
+ * Images up to 2^31 voxels.  Errors: INVALID_ARG (dims, voxel, type, a
+ * periodic axis the image does not span exactly, more than 2^31 voxels, a
+ * second call), OOM, CUDA. */
 int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
                    int32_t nz, double voxel, const double origin[3],
                    double wall_density, double shell_thickness, int32_t wall_type,

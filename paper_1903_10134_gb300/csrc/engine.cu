@@ -1128,7 +1128,7 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
         return h->fail(MDPD_ERR_INVALID_ARG, "wall_density and shell_thickness must be >= 0");
     const int dim[3] = { nx, ny, nz };
     const int64_t nvox = (int64_t)nx * ny * nz;
-    if (nvox > MAX_SCAN) return h->fail(MDPD_ERR_INVALID_ARG, "mask larger than 16.7M voxels");
+    if (nvox > (int64_t(1) << 31)) return h->fail(MDPD_ERR_INVALID_ARG, "mask larger than 2^31 voxels");
     for (int k = 0; k < 3; ++k) {
         if (!h->p.periodic[k]) continue;
         const double span = dim[k] * voxel;
@@ -1150,7 +1150,7 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
     };
     if ((rc = dalloc(h, &dmask, (size_t)nvox)) || (rc = dalloc(h, &cnt, (size_t)nvox * 4)) ||
         (rc = dalloc(h, &off, (size_t)(nvox + 1) * 4)) ||
-        (rc = dalloc(h, &tmp, (size_t)(scan_num_blocks(nvox) + 1) * 4))) {
+        (rc = dalloc(h, &tmp, (size_t)(scan_num_blocks(std::min(nvox, MAX_SCAN)) + 2) * 4))) {
         cleanup();
         return rc;
     }
@@ -1169,7 +1169,10 @@ int mdpd_set_walls(mdpd_handle* h, const uint8_t* solid, int32_t nx, int32_t ny,
     if (ok) {
         launch_mask_pack(st, dmask, nvox, bits);
         launch_wall_count(st, dmask, dim, per, R, R2, lam, k0, k1, cnt);
-        launch_exclusive_scan(st, cnt, nvox, off, tmp);
+        // (masks beyond the two-level scan's limit in segments; the last
+        // word of tmp carries the running total)
+        launch_exclusive_scan_long(st, cnt, nvox, off, tmp,
+                                   tmp + scan_num_blocks(std::min(nvox, MAX_SCAN)) + 1, MAX_SCAN);
         ok = cudaMemcpyAsync(&nw, off + nvox, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
              cudaStreamSynchronize(st) == cudaSuccess;
     }

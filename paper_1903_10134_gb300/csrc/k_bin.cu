@@ -453,6 +453,26 @@ void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* o
                (uint32_t*)nullptr);
 }
 
+__global__ void k_add_carry(uint32_t* __restrict__ out, int64_t len, const uint32_t* __restrict__ carry)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] += *carry;
+}
+
+void launch_exclusive_scan_long(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out,
+                                uint32_t* tmp, uint32_t* carry, int64_t seg)
+{
+    for (int64_t s0 = 0; s0 < n; s0 += seg) {
+        const int64_t len = n - s0 < seg ? n - s0 : seg;
+        // the running total before s0 (written at out[s0] by the previous
+        // segment's fix-up) is saved before this segment's scan overwrites it
+        if (s0 > 0) cudaMemcpyAsync(carry, out + s0, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st);
+        launch_exclusive_scan(st, in + s0, len, out + s0, tmp, false);
+        if (s0 > 0)
+            k_add_carry<<<(unsigned)((len + 1 + 255) / 256), 256, 0, st>>>(out + s0, len + 1, carry);
+    }
+}
+
 void launch_scan_from_sums(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out,
                            const uint32_t* sums, uint32_t* zero_sums)
 {

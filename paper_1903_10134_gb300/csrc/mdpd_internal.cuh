@@ -286,6 +286,11 @@ int scan_num_launches(int64_t n);
 // words; zero_in clears in[] after it is read.
 void launch_exclusive_scan(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out, uint32_t* tmp,
                            bool zero_in = false);
+// The same for any n, as scans of segments of at most seg elements (seg within
+// the two-level scan's limit) joined by a running carry: tmp holds
+// scan_num_blocks(seg) + 1 words and carry one word.
+void launch_exclusive_scan_long(cudaStream_t st, uint32_t* in, int64_t n, uint32_t* out,
+                                uint32_t* tmp, uint32_t* carry, int64_t seg);
 // The same in one launch, given the tile sums (from launch_bin_count); the
 // counts are cleared as they are read, and so is zero_sums (the other tile-sum
 // buffer, for the next binning).

@@ -619,3 +619,32 @@ def test_loaded_positions_wrap_like_the_periodic_rule(M):
         M.mdpd_set_state_accel(s.h, x, np.zeros((n, 3)), np.zeros((n, 3)))
         got = s.state()[0]
     assert np.array_equal(got.view(np.int64), want.view(np.int64))
+
+
+def test_walls_from_a_mask_beyond_one_scan(M):
+    """A voxel image of more voxels (264 x 264 x 256 = 17.8M) than one
+    two-level scan covers (16.7M): the wall counts are scanned in segments
+    joined by a running carry, and the wall particles equal the oracle's
+    placement bit for bit (same ids by ascending voxel id).  The solid part
+    is two slabs, one of them at the far end of the image, whose shell
+    particles come after the segment boundary."""
+    nvox = (256, 264, 264)           # [z, y, x]
+    voxel = 0.5
+    mask = np.zeros(nvox, np.uint8)
+    mask[:6] = 1                     # z < 3: lower wall
+    mask[250:] = 1                   # z >= 125: upper wall (voxels beyond 16.7M)
+    L = (nvox[2] * voxel, nvox[1] * voxel, nvox[0] * voxel)
+    p = I.MDPDParams(box=L, periodic=(1, 1, 1), ntypes=2, frozen_types=(1,), precision=1)
+    rng = np.random.default_rng(12)
+    npart = 2000
+    pos = np.stack([rng.random(npart) * L[0], rng.random(npart) * L[1],
+                    3.5 + rng.random(npart) * 120.0], 1)
+    vel = I.maxwell_velocities(npart, 1.0, rng)
+    with M.System(p, pos, vel, np.zeros(npart, np.int32), 4) as s:
+        s.set_walls(mask, voxel, (0.0, 0.0, 0.0), 6.0, 1.0, 1, 5)
+        wpos, _ = O.place_walls(mask, (1, 1, 1), voxel, (0.0, 0.0, 0.0), 6.0, 1.0, 5)
+        x, _, t, _ = s.state()
+    assert np.prod(nvox) > 4096 * 4096
+    assert x.shape[0] == npart + wpos.shape[0] and wpos.shape[0] > 100000
+    assert np.array_equal(x[npart:], wpos)
+    assert np.all(t[npart:] == 1)
