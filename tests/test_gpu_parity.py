@@ -532,14 +532,15 @@ def test_density_code_shapes_agree_bitwise(M, name, precision):
         s.close()
 
 
-@pytest.mark.parametrize("name", ["rock", "slit"])
+@pytest.mark.parametrize("name", ["rock", "slit", "rock338"])
 def test_full_walled_workload_sampled_parity(M, name):
     """The full-size walled workloads as the bench runs them (FP32, kernels
     picked by the autotuner, frozen split on, a few fused steps): after the
     steps, the densities of all particles (fluid and wall) and the forces of
     a sample of 400 fluid particles at the current step index equal the
-    oracle's at the same state."""
-    w = I.rock() if name == "rock" else I.slit()
+    oracle's at the same state.  rock338 is the 10M-particle rock (a 38.6M
+    voxel image, walls placed by the segmented scan)."""
+    w = I.rock() if name == "rock" else (I.rock(nvox=338) if name == "rock338" else I.slit())
     s = M.System.from_workload(w, precision=1)
     s.autotune()
     s.step(5)
