@@ -455,14 +455,14 @@ void launch_scatter_scalar_by_id(cudaStream_t st, int precision, int n, const ui
                                  const void* rho_sorted, double* out);
 void launch_scatter_type_by_id(cudaStream_t st, int n, const uint32_t* id, const uint8_t* type,
                                int32_t* out);
+// Master state in id order from pos3, vel3 and (if not NULL) acc3, all
+// interleaved xyz; periodic axes wrapped.
 // Set *moved (device word, not cleared here) to 1 if a frozen particle's
 // loaded position (master arrays indexed by id, as k_load_state leaves them)
 // differs in any bit from ref (n x 3, by id), the positions the frozen-frozen
 // density part was computed from.
 void launch_frozen_moved(cudaStream_t st, int n, int64_t cap, const double* x, const double* ref,
                          const uint8_t* type_by_id, uint32_t frozen, uint32_t* moved);
-// Master state in id order from pos3, vel3 and (if not NULL) acc3, all
-// interleaved xyz; periodic axes wrapped.
 void launch_load_state(cudaStream_t st, int n, int64_t cap, const double* pos3,
                        const double* vel3, const double* acc3, const Geo& geo, const Master& m,
                        const uint8_t* type_by_id, uint32_t* status);
